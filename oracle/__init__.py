@@ -1,0 +1,248 @@
+"""Python access to the FP64 CPU oracle of the M_N step (kitrt_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's CPU-baseline leg use
+this module to judge and to time against. The CUDA library never imports or links it, and it
+imports nothing from the CUDA package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import math
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kitrt_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libkitrt_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP if available)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
+        return _OUT
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-D_DEFAULT_SOURCE", _SRC, "-o",
+            _OUT + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True)
+    os.replace(_OUT + ".tmp", _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_bp = C.POINTER(C.c_uint8)
+
+
+def _declare(L):
+    i, d = C.c_int, C.c_double
+    L.orc_gauss_legendre.argtypes = [i, _dp, _dp]
+    L.orc_quad_count.argtypes = [i]
+    L.orc_quadrature.argtypes = [i, _dp, _dp, _dp, _dp, _dp]
+    L.orc_nmom.argtypes = [i]
+    L.orc_basis.argtypes = [i, d, d, _dp]
+    L.orc_tables.argtypes = [i, i, _dp, _dp, _dp, _dp]
+    L.orc_mesh_geometry.argtypes = [i, _dp, i, _ip, _dp, _dp, _dp, _ip, _dp]
+    L.orc_closure_batch.argtypes = [i, i, i, _dp, _dp, _dp, _dp, d, i, i, d, i, i, _ip, _ip]
+    L.orc_isotropic_alpha.argtypes = [i, i, d, _dp, _dp]
+    L.orc_ansatz.argtypes = [i, i, i, _dp, _dp, _dp, i]
+    L.orc_flux_update.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
+                                  d, i, _dp, i]
+    L.orc_mn_run.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, d, i, i,
+                             d, i, i, i, _dp, _dp, _ip]
+    L.orc_mn_adjoint.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _ip, i, _dp, _dp,
+                                 _dp, _bp, d, i, i, d, i, i, _dp, _dp, _dp, _dp, _dp]
+    L.orc_mn_objective.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _ip, _dp, _dp,
+                                   _dp, _bp, d, i, i, d, i, i, _dp, _dp, _dp]
+    L.orc_mlp_forward.argtypes = [i, i, i, i, _dp, _dp, _dp]
+    L.orc_mlp_loss_grad.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp]
+    L.orc_mlp_loss_grad.restype = d
+    L.orc_adam.argtypes = [i, _dp, _dp, _dp, _dp, i, d, d, d, d]
+
+
+def _d(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_ip)
+
+
+def _b(a):
+    assert a.dtype == np.uint8 and a.flags.c_contiguous
+    return a.ctypes.data_as(_bp)
+
+
+def gauss_legendre(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().orc_gauss_legendre(n, _d(x), _d(w))
+    return x, w
+
+
+def nmom(N: int) -> int:
+    return (N + 1) * (N + 2) // 2
+
+
+def quadrature(order: int):
+    Q = 2 * order * order
+    mu, phi, w, ox, oy = (np.zeros(Q) for _ in range(5))
+    lib().orc_quadrature(order, _d(mu), _d(phi), _d(w), _d(ox), _d(oy))
+    return mu, phi, w, ox, oy
+
+
+def basis(N: int, mu: float, phi: float) -> np.ndarray:
+    m = np.zeros(nmom(N))
+    lib().orc_basis(N, float(mu), float(phi), _d(m))
+    return m
+
+
+class Tables:
+    """Full (unfolded) quadrature and basis tables: M [Q, n], w, Omega_x, Omega_y."""
+
+    def __init__(self, N: int, order: int):
+        self.N, self.order = N, order
+        self.n = nmom(N)
+        self.Q = 2 * order * order
+        self.M = np.zeros((self.Q, self.n))
+        self.w = np.zeros(self.Q)
+        self.ox = np.zeros(self.Q)
+        self.oy = np.zeros(self.Q)
+        lib().orc_tables(N, order, _d(self.M), _d(self.w), _d(self.ox), _d(self.oy))
+        self.m0 = 1.0 / math.sqrt(4.0 * math.pi)
+
+
+class Geometry:
+    def __init__(self, xy: np.ndarray, tri: np.ndarray):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        Cc = tri.shape[0]
+        self.C = Cc
+        self.area = np.zeros(Cc)
+        self.perim = np.zeros(Cc)
+        self.cen = np.zeros((Cc, 2))
+        self.nbr = np.zeros((Cc, 3), dtype=np.int32)
+        self.nrm = np.zeros((Cc, 3, 2))
+        rc = lib().orc_mesh_geometry(xy.shape[0], _d(xy), Cc, _i(tri), _d(self.area),
+                                     _d(self.perim), _d(self.cen), _i(self.nbr), _d(self.nrm))
+        if rc != 0:
+            raise ValueError("oracle: degenerate mesh")
+
+    def cfl_dt(self, cfl: float) -> float:
+        return float(cfl * np.min(2.0 * self.area / self.perim))
+
+
+def closure(T: Tables, u: np.ndarray, alpha: np.ndarray, tau=1e-10, max_iter=100, polish=True,
+            nthreads=0, max_halvings=30, c1=1e-4):
+    """Solve the closure for every row of u; alpha is the warm start and is updated in place.
+    Returns (status, iters)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    Cc = u.shape[0]
+    st = np.zeros(Cc, dtype=np.int32)
+    it = np.zeros(Cc, dtype=np.int32)
+    lib().orc_closure_batch(Cc, T.n, T.Q, _d(T.M), _d(T.w), _d(u), _d(alpha), tau, max_iter,
+                            max_halvings, c1, int(polish), nthreads, _i(st), _i(it))
+    return st, it
+
+
+def isotropic_alpha(T: Tables, u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    a = np.zeros_like(u)
+    lib().orc_isotropic_alpha(u.shape[0], T.n, T.m0, _d(u), _d(a))
+    return a
+
+
+def ansatz(T: Tables, alpha: np.ndarray, nthreads=0) -> np.ndarray:
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    psi = np.zeros((alpha.shape[0], T.Q))
+    lib().orc_ansatz(alpha.shape[0], T.n, T.Q, _d(T.M), _d(alpha), _d(psi), nthreads)
+    return psi
+
+
+def flux_update(T: Tables, G: Geometry, psi, u, sigma_a, sigma_s, qsrc, dt, bc=0, nthreads=0):
+    """In-place kinetic flux + source + Euler update of u from the given psi."""
+    lib().orc_flux_update(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                          _d(G.nrm), _d(G.area), _d(np.ascontiguousarray(psi)),
+                          _d(np.ascontiguousarray(sigma_a, dtype=np.float64)),
+                          _d(np.ascontiguousarray(sigma_s, dtype=np.float64)),
+                          _d(np.ascontiguousarray(qsrc, dtype=np.float64)), dt, bc, _d(u),
+                          nthreads)
+
+
+def mn_run(T: Tables, G: Geometry, u, alpha, sigma_a, sigma_s, qsrc, dt, nsteps, bc=0, tau=1e-10,
+           max_iter=100, polish=True, nthreads=0):
+    """nsteps M_N steps in place on u and alpha. Returns (n_failed, status)."""
+    st = np.zeros(G.C, dtype=np.int32)
+    nf = lib().orc_mn_run(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                          _d(G.nrm), _d(G.area),
+                          _d(np.ascontiguousarray(sigma_a, dtype=np.float64)),
+                          _d(np.ascontiguousarray(sigma_s, dtype=np.float64)),
+                          _d(np.ascontiguousarray(qsrc, dtype=np.float64)), dt, bc, nsteps, tau,
+                          max_iter, int(polish), nthreads, _d(u), _d(alpha), _i(st))
+    return nf, st
+
+
+def mn_adjoint(T, G, block_of_cell, sa_blk, ss_blk, qsrc, target, dt, nsteps, u0, alpha0, bc=1,
+               tau=1e-10, max_iter=100, nthreads=0):
+    nb = sa_blk.shape[0]
+    J = np.zeros(1)
+    gsa = np.zeros(nb)
+    gss = np.zeros(nb)
+    nf = lib().orc_mn_adjoint(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                              _d(G.nrm), _d(G.area), _i(block_of_cell), nb, _d(sa_blk),
+                              _d(ss_blk), _d(qsrc), _b(target), dt, bc, nsteps, tau, max_iter,
+                              nthreads, _d(u0), _d(alpha0), _d(J), _d(gsa), _d(gss))
+    if nf:
+        raise RuntimeError(f"oracle adjoint: {nf} failed closures")
+    return float(J[0]), gsa, gss
+
+
+def mn_objective(T, G, block_of_cell, sa_blk, ss_blk, qsrc, target, dt, nsteps, u0, alpha0, bc=1,
+                 tau=1e-10, max_iter=100, nthreads=0):
+    J = np.zeros(1)
+    nf = lib().orc_mn_objective(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                                _d(G.nrm), _d(G.area), _i(block_of_cell), _d(sa_blk), _d(ss_blk),
+                                _d(qsrc), _b(target), dt, bc, nsteps, tau, max_iter, nthreads,
+                                _d(u0), _d(alpha0), _d(J))
+    if nf:
+        raise RuntimeError(f"oracle objective: {nf} failed closures")
+    return float(J[0])
+
+
+def mlp_param_count(din, H, dout):
+    return din * H + H + 2 * (H * H + H) + H * dout + dout
+
+
+def mlp_forward(params, X, din, H, dout):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.zeros((X.shape[0], dout))
+    lib().orc_mlp_forward(X.shape[0], din, H, dout, _d(np.ascontiguousarray(params)), _d(X), _d(Y))
+    return Y
+
+
+def mlp_loss_grad(params, X, T_, din, H, dout):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    T_ = np.ascontiguousarray(T_, dtype=np.float64)
+    g = np.zeros_like(params)
+    loss = lib().orc_mlp_loss_grad(X.shape[0], din, H, dout, _d(np.ascontiguousarray(params)),
+                                   _d(X), _d(T_), _d(g))
+    return loss, g
+
+
+def adam(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    lib().orc_adam(p.shape[0], _d(p), _d(np.ascontiguousarray(g)), _d(m), _d(v), t, lr, b1, b2, eps)
