@@ -1,0 +1,175 @@
+/*
+ * kitrt — C ABI of the GB300 minimal-entropy (M_N) step library.
+ *
+ * The method is the explicit first-order finite-volume M_N scheme of KiT-RT (arXiv 2205.08417):
+ *   - entropy closure with the Maxwell-Boltzmann entropy [Sec. 3.1, Eq. entropyOCP], solved per
+ *     cell through its dual  f(alpha) = <exp(alpha.m)> - alpha.u  by Newton's method with an
+ *     Armijo line search [Sec. 7.2, M_N runs];
+ *   - kinetic upwind flux of the closed ansatz [Sec. 4.4, kinetic numerical flux];
+ *   - isotropic scattering, absorption and source with a forward-Euler update
+ *     [Sec. 3.1 moment equations; Sec. 4.2 explicit first-order iteration].
+ * Angular discretisation: real spherical harmonics of degree N, restricted to the functions even
+ * in mu for the 2D slab geometry [Sec. 3.1, Sec. 3.2], on the tensorised Gauss-Legendre x
+ * uniform-azimuth product rule [Sec. 3.2, Eq. spherical-coordinatesProduct] with `order` Gauss
+ * points and 2*order azimuths (Q = 2 order^2 points; the library folds the +-mu pairs, which share
+ * a 2D direction, into Q' = Q/2 points of doubled weight).
+ *
+ * Conventions
+ *   - Every function returns a kitrt_status code; nothing is thrown across the ABI.
+ *   - "device" pointers are CUDA device memory owned by the caller; "host" pointers are host
+ *     memory. State arrays are row-major, one row per cell: u and alpha are [ncells x nmom] FP64.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls enqueue
+ *     work on it. Calls that must know when every cell's Newton iteration has finished read a
+ *     4-byte counter back to the host and therefore synchronise with `stream` (noted below).
+ *   - The library owns the handles, the angular tables and its workspace (allocated in
+ *     kitrt_mesh_create / kitrt_mn_init, freed by the matching destroy). kitrt_step and
+ *     kitrt_closure allocate nothing.
+ *   - Device kernels never trap: per-cell failures are reported in `status` arrays and in the
+ *     return code.
+ */
+#ifndef KITRT_H
+#define KITRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. Per-cell status values use the same numbers (0 = converged). */
+typedef enum {
+    KITRT_OK = 0,
+    KITRT_EINVAL = 1,          /* bad argument (null pointer, size, unsupported option) */
+    KITRT_ENOTREALIZABLE = 2,  /* a moment vector had no finite minimiser (non-finite values) */
+    KITRT_ENOCONVERGE = 3,     /* a cell hit max_iter Newton iterations */
+    KITRT_ECHOL = 4,           /* Hessian not positive definite in FP64 (Cholesky breakdown) */
+    KITRT_ELINESEARCH = 5,     /* Armijo backtracking exhausted max_halvings */
+    KITRT_ECUDA = 6,           /* a CUDA runtime call failed */
+    KITRT_ENOMEM = 7,          /* device allocation failed */
+    KITRT_ETIMEOUT = 8         /* a bounded device wait expired */
+} kitrt_status;
+
+/* Closure arithmetic. */
+enum {
+    KITRT_FP64 = 0,        /* every sum, factorisation and line search in FP64 */
+    KITRT_MIXED_TF32 = 1,  /* Hessian-only moment sums on tensor cores (TF32 in, FP32 accumulate);
+                              exponent, exp, gradient, objective, Cholesky, line search in FP64 */
+    KITRT_MIXED_BF16 = 2,  /* as MIXED_TF32 with BF16 tensor-core inputs */
+    KITRT_LEARNED = 3      /* MLP prediction of alpha, exact mass fix, FP64 residual check, Newton
+                              (mixed Hessian) only for cells whose residual exceeds fallback_tol */
+};
+
+/* Boundary condition on boundary faces [Sec. 4.4: Neumann and Dirichlet]. */
+enum {
+    KITRT_BC_NEUMANN = 0,  /* zero-gradient ghost: the outside value is the cell's own psi */
+    KITRT_BC_VACUUM = 1    /* Dirichlet psi = 0 outside: boundary faces only let radiation out */
+};
+
+typedef struct kitrt_mesh kitrt_mesh;
+typedef struct kitrt_mn kitrt_mn;
+
+typedef struct {
+    int32_t degree;        /* N >= 0; nmom = (N+1)(N+2)/2; N <= 7 */
+    int32_t quad_order;    /* Gauss points in mu (>= N+1); Q = 2 order^2 */
+    int32_t mode;          /* KITRT_FP64 / KITRT_MIXED_TF32 / KITRT_MIXED_BF16 / KITRT_LEARNED */
+    int32_t bc;            /* KITRT_BC_NEUMANN / KITRT_BC_VACUUM */
+    double tau;            /* Newton stops when ||g||_2 <= tau ||u||_2 (e.g. 1e-10) */
+    int32_t max_iter;      /* Newton iterations per closure (e.g. 100) */
+    int32_t max_halvings;  /* Armijo halvings per iteration (e.g. 30) */
+    double armijo_c1;      /* Armijo constant (e.g. 1e-4) */
+    int32_t polish;        /* 1: one extra full Newton step after the test passes */
+    double cfl;            /* dt = cfl * min_i 2 A_i / P_i when kitrt_step gets dt <= 0 */
+    double fallback_tol;   /* KITRT_LEARNED: accept the MLP when ||<m psi> - u|| <= tol ||u|| */
+} kitrt_mn_params;
+
+/* Counters of the last call (filled only when a non-null pointer is passed; doing so
+ * synchronises with the stream). */
+typedef struct {
+    int64_t closures;      /* cell closures solved (cells x steps) */
+    int64_t evaluations;   /* cell evaluations of the dual (quadrature passes) */
+    int32_t max_evals;     /* largest number of evaluations any cell needed in one closure */
+    int32_t failed;        /* cells whose last closure ended with a non-zero status */
+    int64_t fallbacks;     /* KITRT_LEARNED: cells that needed Newton after the MLP */
+    double dt;             /* time step used */
+} kitrt_stats;
+
+/* Human-readable name of a status code (static string). */
+const char *kitrt_status_string(int32_t code);
+
+/* Fill `p` with the defaults used by the library's tests: N=2, order 10, FP64, Neumann,
+ * tau 1e-10, max_iter 100, 30 halvings, c1 1e-4, polish on, CFL 0.4, fallback_tol 1e-6. */
+int32_t kitrt_default_params(kitrt_mn_params *p);
+
+/* Build a triangle mesh [Sec. 4.1: cell-centred unstructured grid with centroid, area A_i,
+ * neighbours N(i) and face normals n_ij scaled by the face length].
+ *   xy  host [nverts x 2] vertex coordinates; tri host [ntri x 3] vertex indices (either
+ *       orientation; clockwise triangles are reversed). Face k of cell i is the edge from its
+ *       (counter-clockwise) vertex k to vertex k+1.
+ *   out receives the handle. The host arrays are copied; geometry is uploaded to the current
+ *   CUDA device. EINVAL for null pointers, out-of-range indices, zero-area cells or edges shared
+ *   by more than two cells. */
+int32_t kitrt_mesh_create(const double *xy, int32_t nverts, const int32_t *tri, int32_t ntri,
+                          kitrt_mesh **out);
+int32_t kitrt_mesh_destroy(kitrt_mesh *mesh);
+
+/* Copy the mesh geometry to host arrays (any may be NULL): area [C], perimeter [C],
+ * centroid [C x 2], neighbour [C x 3] (-1 = boundary), scaled outward normal [C x 3 x 2];
+ * ncells and the largest stable step min_i 2 A_i / P_i (to be scaled by the CFL number). */
+int32_t kitrt_mesh_geometry(const kitrt_mesh *mesh, int32_t *ncells, double *min_inradius,
+                            double *area, double *perim, double *centroid, int32_t *nbr,
+                            double *nrm);
+
+/* Create an M_N solver on a mesh: builds the folded quadrature, the basis tables and the
+ * workspace for every cell of the mesh (device allocations, owned by the handle). The mesh must
+ * outlive the solver. */
+int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kitrt_mn **out);
+int32_t kitrt_mn_destroy(kitrt_mn *mn);
+
+/* Sizes: moments n, quadrature points Q of the full rule and Q' after folding. */
+int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_t *nquad_folded);
+
+/* Copy the folded quadrature to host arrays (any may be NULL): weights [Q'], 2D directions
+ * [Q' x 2], basis values [Q' x nmom]. */
+int32_t kitrt_mn_quadrature(const kitrt_mn *mn, double *w, double *omega, double *m);
+
+/* Isotropic closed form of the closure: alpha_0 = ln(u_0 / (4 pi m_0)) / m_0, other components
+ * 0 (m_0 = 1/sqrt(4 pi)). u, alpha: device [C x n]. */
+int32_t kitrt_isotropic_alpha(kitrt_mn *mn, const double *u, double *alpha, void *stream);
+
+/* Entropy closure [Sec. 3.1, Eq. entropyOCP] of every cell: alpha minimises
+ * <exp(alpha.m)> - alpha.u on the folded quadrature.
+ *   u      device [C x n], read only.
+ *   alpha  device [C x n]: warm start on input, solution on output (polished if enabled).
+ *   status device [C] int32 per-cell status (0 = converged), or NULL.
+ * Uses the solver's mode (FP64 or MIXED_*; LEARNED closes with its MLP first). Synchronises
+ * with `stream` once per batch of Newton sweeps to test for completion. Returns the first
+ * non-zero per-cell status found, else KITRT_OK. */
+int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
+                      void *stream, kitrt_stats *stats);
+
+/* The closed ansatz at the folded quadrature points: psi [C x Q'] FP64 device,
+ * psi_cq = exp(alpha_c . m_q). */
+int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *stream);
+
+/* nsteps explicit M_N steps, in place:
+ *   u^{n+1}_i = u^n_i - dt/A_i sum_{j in N(i)} F_up(psi_i, psi_j) + dt R_i(u^n_i),
+ *   R_i(u) = -sigma_a,i u - sigma_s,i (u - u_0 e_0) + q_i <m>,
+ * with F_up the kinetic upwind flux of the closed ansatz [Sec. 4.4] and psi the closure of u^n
+ * [Sec. 4.2 explicit iteration; Sec. 3.1: isotropic scattering is diagonal in the moments].
+ *   u       device [C x n]: u^0 in, u^{nsteps} out.
+ *   alpha   device [C x n]: warm start in; out: closure of u^{nsteps-1} (the last closed state).
+ *   sigma_a, sigma_s, q  device [C] per-cell absorption, scattering, isotropic source.
+ *   dt      time step; dt <= 0 selects cfl * min_i 2 A_i / P_i. EINVAL when
+ *           dt * max(sigma_a + sigma_s) > 1 is detectable on the host (not checked on device).
+ *   status  device [C] or NULL: per-cell status of the last failed closure.
+ * Synchronises with `stream` once per step (closure completion test). On a closure failure the
+ * step stops before updating u with that closure and returns its status. */
+int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a,
+                   const double *sigma_s, const double *q, double dt, int32_t nsteps,
+                   int32_t *status, void *stream, kitrt_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KITRT_H */

@@ -1,0 +1,575 @@
+// kitrt host side: mesh construction, angular tables, workspace, and the C ABI entry points.
+//
+// Mesh [Sec. 4.1]: cell-centred triangles with area, neighbours and length-scaled outward
+// normals. Angular tables [Sec. 3.1, Sec. 3.2]: product quadrature (Gauss-Legendre in mu x
+// uniform azimuth), real spherical harmonics even in mu, folded over +-mu. The Hessian of the
+// dual is assembled from moments against the degree-2N basis through Gaunt coefficients
+// <m_a m_b m~_c>, which is exact because a product of two harmonics of degree <= N is a
+// combination of harmonics of degree <= 2N (and stays even in mu).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
+#include "kitrt_internal.cuh"
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+#define CUDA_OK(x)                                   \
+    do {                                             \
+        if ((x) != cudaSuccess) return KITRT_ECUDA; \
+    } while (0)
+
+// Gauss-Legendre rule on [-1,1] (ascending nodes): Newton iteration on P_n(x), evaluated by the
+// Bonnet recurrence, from Tricomi's initial approximation of the k-th root.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int k = 1; k <= n; ++k) {
+        double th = kPi * (4.0 * k - 1.0) / (4.0 * n + 2.0);
+        double r = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * cos(th);
+        double dpn = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double pm = 1.0, pc = r;
+            for (int j = 2; j <= n; ++j) {
+                double pn = ((2 * j - 1) * r * pc - (j - 1) * pm) / j;
+                pm = pc;
+                pc = pn;
+            }
+            if (n == 1) pm = 1.0, pc = r;
+            dpn = n * (pm - r * pc) / (1.0 - r * r);
+            double step = pc / dpn;
+            r -= step;
+            if (fabs(step) <= 1e-17) break;
+        }
+        double pm = 1.0, pc = r;
+        for (int j = 2; j <= n; ++j) {
+            double pn = ((2 * j - 1) * r * pc - (j - 1) * pm) / j;
+            pm = pc;
+            pc = pn;
+        }
+        dpn = n * (pm - r * pc) / (1.0 - r * r);
+        // root k counted from +1 downwards
+        x[n - k] = r;
+        w[n - k] = 2.0 / ((1.0 - r * r) * dpn * dpn);
+    }
+}
+
+// Fully normalised associated Legendre values Pn[l][k] = N_l^k P_l^k(mu) (no Condon-Shortley
+// phase) for 0 <= k <= l <= L, by the standard stable recurrences in l.
+void norm_legendre(int L, double mu, double Pn[][24])
+{
+    double s = sqrt(fmax(0.0, 1.0 - mu * mu));
+    Pn[0][0] = 1.0 / sqrt(4.0 * kPi);
+    for (int k = 1; k <= L; ++k) Pn[k][k] = sqrt((2.0 * k + 1.0) / (2.0 * k)) * s * Pn[k - 1][k - 1];
+    for (int k = 0; k < L; ++k) Pn[k + 1][k] = sqrt(2.0 * k + 3.0) * mu * Pn[k][k];
+    for (int k = 0; k <= L; ++k)
+        for (int l = k + 2; l <= L; ++l) {
+            double a = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)k * k));
+            double b = sqrt((((l - 1.0) * (l - 1.0)) - (double)k * k) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+            Pn[l][k] = a * (mu * Pn[l - 1][k] - b * Pn[l - 2][k]);
+        }
+}
+
+// 2D basis of degree L at (mu, phi): real harmonics m_l^k with l + |k| even, ordered by l then k.
+int basis2d(int L, double mu, double phi, double *out)
+{
+    double Pn[24][24];
+    norm_legendre(L, mu, Pn);
+    int i = 0;
+    for (int l = 0; l <= L; ++l)
+        for (int k = -l; k <= l; ++k) {
+            int ak = k < 0 ? -k : k;
+            if ((l + ak) % 2) continue;
+            double v = Pn[l][ak];
+            if (k > 0) v *= sqrt(2.0) * cos(k * phi);
+            if (k < 0) v *= sqrt(2.0) * sin(ak * phi);
+            out[i++] = v;
+        }
+    return i;
+}
+
+int nmom_of(int L) { return (L + 1) * (L + 2) / 2; }
+
+// Folded product rule: pairs of Gauss nodes +-mu share the 2D direction and every basis value,
+// so they merge into one point of doubled weight (an odd order keeps mu = 0 once).
+struct FoldedRule {
+    std::vector<double> mu, phi, w;
+};
+
+FoldedRule folded_rule(int order)
+{
+    std::vector<double> x, gw;
+    gauss_legendre(order, x, gw);
+    const int nphi = 2 * order, half = order / 2;
+    FoldedRule r;
+    auto add_ring = [&](double mu, double wk) {
+        for (int l = 1; l <= nphi; ++l) {
+            r.mu.push_back(mu);
+            r.phi.push_back(l * (2.0 * kPi / nphi));
+            r.w.push_back(wk * 2.0 * kPi / nphi);
+        }
+    };
+    // nodes are ascending: k = order-1 .. order-half are the positive ones, paired with order-1-k
+    for (int k = order - 1; k >= order - half; --k) add_ring(x[k], gw[k] + gw[order - 1 - k]);
+    if (order % 2) add_ring(0.0, gw[half]);
+    return r;
+}
+
+template <typename T>
+int dev_upload(kitrt_mn *mn, T **dst, const std::vector<T> &src)
+{
+    size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    if (cudaMalloc((void **)dst, bytes) != cudaSuccess) return KITRT_ENOMEM;
+    mn->allocs.push_back(*dst);
+    if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(T),
+                                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return KITRT_ECUDA;
+    return KITRT_OK;
+}
+
+template <typename T>
+int dev_alloc(kitrt_mn *mn, T **dst, size_t count)
+{
+    if (cudaMalloc((void **)dst, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess)
+        return KITRT_ENOMEM;
+    mn->allocs.push_back(*dst);
+    return KITRT_OK;
+}
+
+}  // namespace
+
+Tables kitrt_mn::tables() const
+{
+    Tables T;
+    T.n = n;
+    T.n2 = n2;
+    T.Qf = Qf;
+    T.Qp = Qp;
+    T.m0 = 1.0 / sqrt(4.0 * kPi);
+    T.Mt = d_Mt;
+    T.w = d_w;
+    T.wox = d_wox;
+    T.woy = d_woy;
+    T.mbar = d_mbar;
+    T.gstart = d_gstart;
+    T.gidx = d_gidx;
+    T.gcoef = d_gcoef;
+    T.Mt32 = d_Mt32;
+    T.w32 = d_w32;
+    return T;
+}
+
+extern "C" {
+
+const char *kitrt_status_string(int32_t code)
+{
+    switch (code) {
+    case KITRT_OK: return "ok";
+    case KITRT_EINVAL: return "invalid argument";
+    case KITRT_ENOTREALIZABLE: return "moment vector not realizable (non-finite closure)";
+    case KITRT_ENOCONVERGE: return "Newton iteration limit reached";
+    case KITRT_ECHOL: return "Hessian not positive definite (Cholesky breakdown)";
+    case KITRT_ELINESEARCH: return "line search exhausted";
+    case KITRT_ECUDA: return "CUDA runtime error";
+    case KITRT_ENOMEM: return "device allocation failed";
+    case KITRT_ETIMEOUT: return "bounded device wait expired";
+    default: return "unknown status";
+    }
+}
+
+int32_t kitrt_default_params(kitrt_mn_params *p)
+{
+    if (!p) return KITRT_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->degree = 2;
+    p->quad_order = 10;
+    p->mode = KITRT_FP64;
+    p->bc = KITRT_BC_NEUMANN;
+    p->tau = 1e-10;
+    p->max_iter = 100;
+    p->max_halvings = 30;
+    p->armijo_c1 = 1e-4;
+    p->polish = 1;
+    p->cfl = 0.4;
+    p->fallback_tol = 1e-6;
+    return KITRT_OK;
+}
+
+int32_t kitrt_mesh_create(const double *xy, int32_t nverts, const int32_t *tri, int32_t ntri,
+                          kitrt_mesh **out)
+{
+    if (!xy || !tri || !out || nverts < 3 || ntri < 1) return KITRT_EINVAL;
+    *out = nullptr;
+    kitrt_mesh *m = new kitrt_mesh();
+    m->C = ntri;
+    cudaGetDevice(&m->device);
+    m->area.resize(ntri);
+    m->perim.resize(ntri);
+    m->cen.resize(2 * (size_t)ntri);
+    m->nrm.resize(6 * (size_t)ntri);
+    m->nbr.assign(3 * (size_t)ntri, -1);
+    std::unordered_map<uint64_t, int64_t> open_edge;  // edge key -> cell*3+face
+    open_edge.reserve((size_t)ntri * 2);
+    double minr = 1e300;
+    int rc = KITRT_OK;
+    for (int32_t c = 0; c < ntri && rc == KITRT_OK; ++c) {
+        int32_t v0 = tri[3 * c], v1 = tri[3 * c + 1], v2 = tri[3 * c + 2];
+        if (v0 < 0 || v1 < 0 || v2 < 0 || v0 >= nverts || v1 >= nverts || v2 >= nverts) {
+            rc = KITRT_EINVAL;
+            break;
+        }
+        double ax = xy[2 * v0], ay = xy[2 * v0 + 1];
+        double cross = (xy[2 * v1] - ax) * (xy[2 * v2 + 1] - ay) - (xy[2 * v2] - ax) * (xy[2 * v1 + 1] - ay);
+        if (cross < 0) std::swap(v1, v2);
+        cross = fabs(cross);
+        if (!(cross > 0.0)) {
+            rc = KITRT_EINVAL;
+            break;
+        }
+        int32_t v[3] = {v0, v1, v2};
+        m->area[c] = 0.5 * cross;
+        m->cen[2 * c] = (xy[2 * v0] + xy[2 * v1] + xy[2 * v2]) / 3.0;
+        m->cen[2 * c + 1] = (xy[2 * v0 + 1] + xy[2 * v1 + 1] + xy[2 * v2 + 1]) / 3.0;
+        double per = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            int32_t a = v[k], b = v[(k + 1) % 3];
+            double dx = xy[2 * b] - xy[2 * a], dy = xy[2 * b + 1] - xy[2 * a + 1];
+            // outward normal of edge a->b of a counter-clockwise triangle, |n| = edge length
+            m->nrm[6 * (size_t)c + 2 * k] = xy[2 * b + 1] - xy[2 * a + 1];
+            m->nrm[6 * (size_t)c + 2 * k + 1] = xy[2 * a] - xy[2 * b];
+            per += sqrt(dx * dx + dy * dy);
+            uint64_t lo = (uint64_t)std::min(a, b), hi = (uint64_t)std::max(a, b);
+            uint64_t key = (lo << 32) | hi;
+            auto it = open_edge.find(key);
+            if (it == open_edge.end()) {
+                open_edge.emplace(key, (int64_t)c * 3 + k);
+            } else {
+                int64_t other = it->second;
+                if (other < 0) {
+                    rc = KITRT_EINVAL;  // third cell on one edge
+                    break;
+                }
+                int32_t oc = (int32_t)(other / 3), ok = (int32_t)(other % 3);
+                m->nbr[3 * (size_t)c + k] = oc;
+                m->nbr[3 * (size_t)oc + ok] = c;
+                it->second = -1;
+            }
+        }
+        m->perim[c] = per;
+        minr = std::min(minr, 2.0 * m->area[c] / per);
+    }
+    if (rc != KITRT_OK) {
+        delete m;
+        return rc;
+    }
+    m->min_inradius = minr;
+    std::vector<int4> nb4(ntri);
+    for (int32_t c = 0; c < ntri; ++c)
+        nb4[c] = make_int4(m->nbr[3 * c], m->nbr[3 * c + 1], m->nbr[3 * c + 2], 0);
+    bool ok = cudaMalloc(&m->d_nbr, sizeof(int4) * ntri) == cudaSuccess &&
+              cudaMalloc(&m->d_nrm, sizeof(double) * 6 * ntri) == cudaSuccess &&
+              cudaMalloc(&m->d_area, sizeof(double) * ntri) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_nbr, nb4.data(), sizeof(int4) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_nrm, m->nrm.data(), sizeof(double) * 6 * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_area, m->area.data(), sizeof(double) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        kitrt_mesh_destroy(m);
+        return KITRT_ENOMEM;
+    }
+    *out = m;
+    return KITRT_OK;
+}
+
+int32_t kitrt_mesh_destroy(kitrt_mesh *m)
+{
+    if (!m) return KITRT_EINVAL;
+    cudaFree(m->d_nbr);
+    cudaFree(m->d_nrm);
+    cudaFree(m->d_area);
+    delete m;
+    return KITRT_OK;
+}
+
+int32_t kitrt_mesh_geometry(const kitrt_mesh *m, int32_t *ncells, double *min_inradius,
+                            double *area, double *perim, double *centroid, int32_t *nbr,
+                            double *nrm)
+{
+    if (!m) return KITRT_EINVAL;
+    size_t C = m->C;
+    if (ncells) *ncells = m->C;
+    if (min_inradius) *min_inradius = m->min_inradius;
+    if (area) memcpy(area, m->area.data(), C * sizeof(double));
+    if (perim) memcpy(perim, m->perim.data(), C * sizeof(double));
+    if (centroid) memcpy(centroid, m->cen.data(), 2 * C * sizeof(double));
+    if (nbr) memcpy(nbr, m->nbr.data(), 3 * C * sizeof(int32_t));
+    if (nrm) memcpy(nrm, m->nrm.data(), 6 * C * sizeof(double));
+    return KITRT_OK;
+}
+
+int32_t kitrt_mn_destroy(kitrt_mn *mn)
+{
+    if (!mn) return KITRT_EINVAL;
+    for (void *p : mn->allocs) cudaFree(p);
+    if (mn->h_cnt) cudaFreeHost(mn->h_cnt);
+    delete mn;
+    return KITRT_OK;
+}
+
+int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kitrt_mn **out)
+{
+    if (!mesh || !params || !out) return KITRT_EINVAL;
+    *out = nullptr;
+    const kitrt_mn_params &p = *params;
+    if (p.degree < 1 || p.degree > KITRT_MAX_DEGREE || p.quad_order < p.degree + 1 ||
+        p.quad_order > 64 || !(p.tau > 0) || p.max_iter < 1 || p.max_halvings < 0 ||
+        p.mode < KITRT_FP64 || p.mode > KITRT_LEARNED || (p.bc != 0 && p.bc != 1))
+        return KITRT_EINVAL;
+    kitrt_mn *mn = new kitrt_mn();
+    mn->mesh = mesh;
+    mn->p = p;
+    mn->N = p.degree;
+    mn->n = nmom_of(p.degree);
+    mn->n2 = nmom_of(2 * p.degree);
+    mn->npairs = mn->n * (mn->n + 1) / 2;
+    mn->Q = 2 * p.quad_order * p.quad_order;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&mn->nsm, cudaDevAttrMultiProcessorCount, dev);
+    int rc;
+#define TRY(x)                    \
+    do {                          \
+        rc = (x);                 \
+        if (rc != KITRT_OK) {     \
+            kitrt_mn_destroy(mn); \
+            return rc;            \
+        }                         \
+    } while (0)
+
+    // folded quadrature and tables
+    FoldedRule r = folded_rule(p.quad_order);
+    mn->Qf = (int)r.w.size();
+    mn->Qp = (mn->Qf + 31) / 32 * 32;
+    const int n = mn->n, n2 = mn->n2, Qp = mn->Qp, Qf = mn->Qf;
+    std::vector<double> Mt((size_t)n2 * Qp, 0.0), w(Qp, 0.0), wox(Qp, 0.0), woy(Qp, 0.0);
+    mn->h_w.resize(Qf);
+    mn->h_ox.resize(Qf);
+    mn->h_oy.resize(Qf);
+    mn->h_M.resize((size_t)Qf * n);
+    std::vector<double> mb(n, 0.0);
+    double tmp[128];
+    for (int q = 0; q < Qf; ++q) {
+        double s = sqrt(1.0 - r.mu[q] * r.mu[q]);
+        double ox = s * sin(r.phi[q]), oy = s * cos(r.phi[q]);
+        basis2d(2 * mn->N, r.mu[q], r.phi[q], tmp);
+        for (int c = 0; c < n2; ++c) Mt[(size_t)c * Qp + q] = tmp[c];
+        for (int a = 0; a < n; ++a) mn->h_M[(size_t)q * n + a] = tmp[a];
+        w[q] = r.w[q];
+        wox[q] = r.w[q] * ox;
+        woy[q] = r.w[q] * oy;
+        mn->h_w[q] = r.w[q];
+        mn->h_ox[q] = ox;
+        mn->h_oy[q] = oy;
+        for (int a = 0; a < n; ++a) mb[a] += r.w[q] * tmp[a];
+    }
+    // Gaunt coefficients G[(a,b),c] = <m_a m_b m~_c> on a rule exact for degree 4N
+    FoldedRule g = folded_rule(2 * mn->N + 2);
+    std::vector<double> G((size_t)mn->npairs * n2, 0.0);
+    for (size_t q = 0; q < g.w.size(); ++q) {
+        basis2d(2 * mn->N, g.mu[q], g.phi[q], tmp);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b <= a; ++b) {
+                double ab = g.w[q] * tmp[a] * tmp[b];
+                double *row = &G[(size_t)(a * (a + 1) / 2 + b) * n2];
+                for (int c = 0; c < n2; ++c) row[c] += ab * tmp[c];
+            }
+    }
+    std::vector<int32_t> gstart(mn->npairs + 1, 0), gidx;
+    std::vector<double> gcoef;
+    for (int pp = 0; pp < mn->npairs; ++pp) {
+        gstart[pp] = (int32_t)gidx.size();
+        for (int c = 0; c < n2; ++c) {
+            double v = G[(size_t)pp * n2 + c];
+            if (fabs(v) > 1e-12) {
+                gidx.push_back(c);
+                gcoef.push_back(v);
+            }
+        }
+    }
+    gstart[mn->npairs] = (int32_t)gidx.size();
+    std::vector<float> Mt32(Mt.begin(), Mt.end()), w32(w.begin(), w.end());
+    TRY(dev_upload(mn, &mn->d_Mt, Mt));
+    TRY(dev_upload(mn, &mn->d_w, w));
+    TRY(dev_upload(mn, &mn->d_wox, wox));
+    TRY(dev_upload(mn, &mn->d_woy, woy));
+    TRY(dev_upload(mn, &mn->d_mbar, mb));
+    TRY(dev_upload(mn, &mn->d_gstart, gstart));
+    TRY(dev_upload(mn, &mn->d_gidx, gidx));
+    TRY(dev_upload(mn, &mn->d_gcoef, gcoef));
+    TRY(dev_upload(mn, &mn->d_Mt32, Mt32));
+    TRY(dev_upload(mn, &mn->d_w32, w32));
+
+    // workspace
+    const size_t C = mesh->C;
+    NewtonState &S = mn->st;
+    TRY(dev_alloc(mn, &S.alpha, C * n));
+    TRY(dev_alloc(mn, &S.dir, C * n));
+    TRY(dev_alloc(mn, &S.U, C * n));
+    TRY(dev_alloc(mn, &S.fsum, C));
+    TRY(dev_alloc(mn, &S.f0, C));
+    TRY(dev_alloc(mn, &S.gd, C));
+    TRY(dev_alloc(mn, &S.L, C * mn->npairs));
+    TRY(dev_alloc(mn, &S.lam, C));
+    TRY(dev_alloc(mn, &S.phase, C));
+    TRY(dev_alloc(mn, &S.iters, C));
+    TRY(dev_alloc(mn, &S.halv, C));
+    TRY(dev_alloc(mn, &S.evals, C));
+    TRY(dev_alloc(mn, &S.status, C));
+    TRY(dev_alloc(mn, &S.list[0], C));
+    TRY(dev_alloc(mn, &S.list[1], C));
+    TRY(dev_alloc(mn, &S.cnt, 8));
+    TRY(dev_alloc(mn, &mn->d_psi, C * Qp));
+    if (cudaMallocHost(&mn->h_cnt, 8 * sizeof(int32_t)) != cudaSuccess) {
+        kitrt_mn_destroy(mn);
+        return KITRT_ENOMEM;
+    }
+#undef TRY
+    *out = mn;
+    return KITRT_OK;
+}
+
+int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_t *nquad_folded)
+{
+    if (!mn) return KITRT_EINVAL;
+    if (nmom) *nmom = mn->n;
+    if (nquad) *nquad = mn->Q;
+    if (nquad_folded) *nquad_folded = mn->Qf;
+    return KITRT_OK;
+}
+
+int32_t kitrt_mn_quadrature(const kitrt_mn *mn, double *w, double *omega, double *m)
+{
+    if (!mn) return KITRT_EINVAL;
+    for (int q = 0; q < mn->Qf; ++q) {
+        if (w) w[q] = mn->h_w[q];
+        if (omega) {
+            omega[2 * q] = mn->h_ox[q];
+            omega[2 * q + 1] = mn->h_oy[q];
+        }
+    }
+    if (m) memcpy(m, mn->h_M.data(), sizeof(double) * mn->h_M.size());
+    return KITRT_OK;
+}
+
+int32_t kitrt_isotropic_alpha(kitrt_mn *mn, const double *u, double *alpha, void *stream)
+{
+    if (!mn || !u || !alpha) return KITRT_EINVAL;
+    return launch_isotropic(mn->tables(), mn->mesh->C, u, alpha, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Newton driver (shared by kitrt_closure and kitrt_step)
+// ------------------------------------------------------------------------------------------
+
+// Runs the closure of every cell to completion. first = 1 starts from alpha_in (evaluation
+// first); first = 0 reuses the state of the previous closure as the predictor. Leaves the
+// converged state in mn->st; returns the first failure status or KITRT_OK.
+static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, int first,
+                       cudaStream_t s, kitrt_stats *stats)
+{
+    const int C = mn->mesh->C;
+    const Tables T = mn->tables();
+    NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, mn->p.polish};
+    CUDA_OK(cudaMemsetAsync(mn->st.cnt, 0, 8 * sizeof(int32_t), s));
+    int rc = launch_begin(mn, T, mn->st, C, u, alpha_in, first, np, s);
+    if (rc) return rc;
+    const int batch = 4;
+    const int max_launch = (mn->p.max_iter + 1) * (mn->p.max_halvings + 1) + 1;
+    int k = 0;
+    for (;;) {
+        for (int b = 0; b < batch; ++b, ++k) {
+            rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s);
+            if (rc) return rc;
+        }
+        CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaStreamSynchronize(s));
+        int active = mn->h_cnt[k % 3];
+        if (active == 0) break;
+        if (k >= max_launch) return KITRT_ETIMEOUT;
+    }
+    if (stats) {
+        stats->closures += C;
+        stats->max_evals = std::max(stats->max_evals, mn->h_cnt[4]);
+        stats->failed = mn->h_cnt[3];
+    }
+    if (mn->h_cnt[3] > 0) {
+        // report the first failing code
+        std::vector<int32_t> stv(C);
+        CUDA_OK(cudaMemcpy(stv.data(), mn->st.status, sizeof(int32_t) * C, cudaMemcpyDeviceToHost));
+        for (int32_t v : stv)
+            if (v) return v;
+    }
+    return KITRT_OK;
+}
+
+extern "C" {
+
+int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
+                      void *stream, kitrt_stats *stats)
+{
+    if (!mn || !u || !alpha) return KITRT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    int rc = run_closure(mn, u, alpha, 1, s, stats);
+    int rc2 = launch_finish(mn, mn->tables(), mn->st, mn->mesh->C, alpha, nullptr, nullptr,
+                            mn->p.polish, s);
+    if (status)
+        CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * mn->mesh->C,
+                                cudaMemcpyDeviceToDevice, s));
+    if (stats) CUDA_OK(cudaStreamSynchronize(s));
+    return rc ? rc : rc2;
+}
+
+int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *stream)
+{
+    if (!mn || !alpha || !psi) return KITRT_EINVAL;
+    return launch_ansatz(mn->tables(), mn->mesh->C, alpha, psi, (cudaStream_t)stream);
+}
+
+int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a,
+                   const double *sigma_s, const double *q, double dt, int32_t nsteps,
+                   int32_t *status, void *stream, kitrt_stats *stats)
+{
+    if (!mn || !u || !alpha || !sigma_a || !sigma_s || !q || nsteps < 0) return KITRT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dt <= 0.0) dt = mn->p.cfl * mn->mesh->min_inradius;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->dt = dt;
+    }
+    const int C = mn->mesh->C;
+    const Tables T = mn->tables();
+    int rc = KITRT_OK;
+    for (int32_t it = 0; it < nsteps; ++it) {
+        rc = run_closure(mn, u, alpha, it == 0, s, stats);
+        if (rc) break;
+        rc = launch_finish(mn, T, mn->st, C, alpha, mn->d_psi, nullptr, mn->p.polish, s);
+        if (rc) break;
+        rc = launch_flux_update(mn, T, C, mn->d_psi, nullptr, u, sigma_a, sigma_s, q, dt, mn->p.bc, s);
+        if (rc) break;
+    }
+    if (status)
+        CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * C,
+                                cudaMemcpyDeviceToDevice, s));
+    if (stats) CUDA_OK(cudaStreamSynchronize(s));
+    return rc;
+}
+
+}  // extern "C"

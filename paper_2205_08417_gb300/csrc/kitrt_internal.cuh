@@ -1,0 +1,100 @@
+// Internal declarations of the kitrt library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "kitrt.h"
+
+#define KITRT_MAX_DEGREE 5
+#define KITRT_MAX_NMOM 21     // (5+1)(5+2)/2
+#define KITRT_MAX_NMOM2 66    // degree-10 2D basis: (10+1)(10+2)/2
+
+// Per-cell Newton phase.
+enum : int32_t { PH_DONE = 0, PH_INIT = 1, PH_NEWTON = 2 };
+
+struct kitrt_mesh {
+    int32_t C = 0;
+    int device = 0;
+    double min_inradius = 0.0;
+    std::vector<double> area, perim, cen, nrm;
+    std::vector<int32_t> nbr;
+    int4 *d_nbr = nullptr;     // [C] neighbours across faces 0..2 (-1 = boundary), .w unused
+    double *d_nrm = nullptr;   // [C x 6] scaled outward normals (nx0, ny0, nx1, ny1, nx2, ny2)
+    double *d_area = nullptr;  // [C]
+};
+
+// Device views handed to kernels by value.
+struct Tables {
+    int n, n2, Qf, Qp;        // moments, degree-2N moments, folded points, padded points
+    double m0;                // m_0 = 1/sqrt(4 pi)
+    const double *Mt;         // [n2 x Qp] extended basis at folded points (first n rows = basis)
+    const double *w;          // [Qp] folded weights (0 on padding)
+    const double *wox, *woy;  // [Qp] w * Omega_x, w * Omega_y
+    const double *mbar;       // [n] sum_q w_q m_q
+    const int32_t *gstart;    // [npairs + 1] Gaunt term ranges per packed pair (a >= b)
+    const int32_t *gidx;      // [nnz] extended-moment index c
+    const double *gcoef;      // [nnz] <m_a m_b m~_c>
+    const float *Mt32;        // [n2 x Qp] FP32 copy
+    const float *w32;
+};
+
+struct NewtonState {
+    double *alpha;     // [C x n] current iterate alpha_k (pre-polish)
+    double *dir;       // [C x n] Newton direction at alpha_k (polish direction once converged)
+    double *U;         // [C x n] moments <m exp(alpha_k.m)>
+    double *fsum;      // [C] <exp(alpha_k.m)>
+    double *f0;        // [C] f(alpha_k; u) for the Armijo test
+    double *gd;        // [C] g(alpha_k).dir
+    double *L;         // [C x npairs] packed lower Cholesky factor of H(alpha_k)
+    double *lam;       // [C] line-search step
+    int32_t *phase;    // [C]
+    int32_t *iters;    // [C] accepted Newton iterations in this closure
+    int32_t *halv;     // [C] halvings in the current iteration
+    int32_t *evals;    // [C] evaluations in this closure
+    int32_t *status;   // [C]
+    int32_t *list[2];  // active cell lists (ping-pong)
+    int32_t *cnt;      // [8]: cnt[0..2] rotating list counters, cnt[3] failures, cnt[4] max evals,
+                       //       cnt[5] fallbacks
+};
+
+struct NewtonParams {
+    double tau, c1;
+    int max_iter, max_halvings, polish;
+};
+
+struct kitrt_mn {
+    const kitrt_mesh *mesh = nullptr;
+    kitrt_mn_params p{};
+    int N = 0, n = 0, n2 = 0, npairs = 0, Q = 0, Qf = 0, Qp = 0;
+    int nsm = 0;
+    std::vector<double> h_w, h_ox, h_oy, h_M;  // folded tables (host copies; M is [Qf x n])
+    // device tables
+    double *d_Mt = nullptr, *d_w = nullptr, *d_wox = nullptr, *d_woy = nullptr;
+    double *d_mbar = nullptr, *d_gcoef = nullptr;
+    int32_t *d_gstart = nullptr, *d_gidx = nullptr;
+    float *d_Mt32 = nullptr, *d_w32 = nullptr;
+    // workspace
+    NewtonState st{};
+    double *d_psi = nullptr;   // [C x Qp] FP64 ansatz
+    float *d_psi32 = nullptr;  // [C x Qp] FP32 ansatz (mixed modes)
+    int32_t *h_cnt = nullptr;  // pinned copy of st.cnt
+    std::vector<void *> allocs;
+    Tables tables() const;
+};
+
+// Kernel launchers (closure_fp64.cu, flux.cu).
+int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cudaStream_t s);
+int launch_begin(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+                 const double *u, const double *alpha_in, int first, NewtonParams np,
+                 cudaStream_t s);
+int launch_eval_fp64(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+                     const double *u, int k, NewtonParams np, cudaStream_t s);
+int launch_finish(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+                  double *alpha_out, double *psi, float *psi32, int polish, cudaStream_t s);
+int launch_ansatz(const Tables &T, int C, const double *alpha, double *psi, cudaStream_t s);
+int launch_flux_update(const kitrt_mn *mn, const Tables &T, int C, const double *psi,
+                       const float *psi32, double *u, const double *sa, const double *ss,
+                       const double *q, double dt, int bc, cudaStream_t s);

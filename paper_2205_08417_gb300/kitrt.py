@@ -1,0 +1,232 @@
+"""Thin Python binding of the kitrt C ABI (include/kitrt.h).
+
+Argument marshalling only: every step of the M_N path runs in the library's CUDA kernels. Device
+arrays are torch CUDA tensors (the library reads their data pointers); work is enqueued on
+torch's current stream. There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KITRT_OK = 0
+STATUS_NAMES = {0: "ok", 1: "EINVAL", 2: "ENOTREALIZABLE", 3: "ENOCONVERGE", 4: "ECHOL",
+                5: "ELINESEARCH", 6: "ECUDA", 7: "ENOMEM", 8: "ETIMEOUT"}
+MODES = {"fp64": 0, "mixed_tf32": 1, "mixed_bf16": 2, "learned": 3}
+BCS = {"neumann": 0, "vacuum": 1}
+
+
+class KitrtError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} ({_lib().kitrt_status_string(code).decode()})")
+
+
+class Params(C.Structure):
+    _fields_ = [("degree", C.c_int32), ("quad_order", C.c_int32), ("mode", C.c_int32),
+                ("bc", C.c_int32), ("tau", C.c_double), ("max_iter", C.c_int32),
+                ("max_halvings", C.c_int32), ("armijo_c1", C.c_double), ("polish", C.c_int32),
+                ("cfl", C.c_double), ("fallback_tol", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("closures", C.c_int64), ("evaluations", C.c_int64), ("max_evals", C.c_int32),
+                ("failed", C.c_int32), ("fallbacks", C.c_int64), ("dt", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+# name -> (restype, argtypes); kept in the order of include/kitrt.h
+SIGNATURES = {
+    "kitrt_status_string": (C.c_char_p, [C.c_int32]),
+    "kitrt_default_params": (C.c_int32, [C.POINTER(Params)]),
+    "kitrt_mesh_create": (C.c_int32, [_dp, C.c_int32, _ip, C.c_int32, C.POINTER(_vp)]),
+    "kitrt_mesh_destroy": (C.c_int32, [_vp]),
+    "kitrt_mesh_geometry": (C.c_int32, [_vp, _ip, _dp, _dp, _dp, _dp, _ip, _dp]),
+    "kitrt_mn_init": (C.c_int32, [_vp, C.POINTER(Params), C.POINTER(_vp)]),
+    "kitrt_mn_destroy": (C.c_int32, [_vp]),
+    "kitrt_mn_sizes": (C.c_int32, [_vp, _ip, _ip, _ip]),
+    "kitrt_mn_quadrature": (C.c_int32, [_vp, _dp, _dp, _dp]),
+    "kitrt_isotropic_alpha": (C.c_int32, [_vp, _vp, _vp, _vp]),
+    "kitrt_closure": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Stats)]),
+    "kitrt_ansatz": (C.c_int32, [_vp, _vp, _vp, _vp]),
+    "kitrt_step": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int32, _vp, _vp,
+                               C.POINTER(Stats)]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"kitrt CUDA library not built ({path}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc: int, where: str):
+    if rc != KITRT_OK:
+        raise KitrtError(rc, where)
+
+
+def _dev(t, dtype=None):
+    """Data pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("kitrt expects contiguous CUDA tensors")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"kitrt expects {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _np_d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _np_i(a):
+    return a.ctypes.data_as(_ip)
+
+
+class Mesh:
+    """Triangle mesh handle (kitrt_mesh_create)."""
+
+    def __init__(self, xy: np.ndarray, tri: np.ndarray):
+        self._xy = np.ascontiguousarray(xy, dtype=np.float64)
+        self._tri = np.ascontiguousarray(tri, dtype=np.int32)
+        h = C.c_void_p()
+        _check(_lib().kitrt_mesh_create(_np_d(self._xy), self._xy.shape[0], _np_i(self._tri),
+                                        self._tri.shape[0], C.byref(h)), "kitrt_mesh_create")
+        self.handle = h
+        self.ncells = int(self._tri.shape[0])
+
+    def geometry(self):
+        Cc = self.ncells
+        area, perim = np.zeros(Cc), np.zeros(Cc)
+        cen, nbr, nrm = np.zeros((Cc, 2)), np.zeros((Cc, 3), np.int32), np.zeros((Cc, 3, 2))
+        nc = C.c_int32()
+        mr = C.c_double()
+        _check(_lib().kitrt_mesh_geometry(self.handle, C.byref(nc), C.byref(mr), _np_d(area),
+                                          _np_d(perim), _np_d(cen), _np_i(nbr), _np_d(nrm)),
+               "kitrt_mesh_geometry")
+        return dict(area=area, perim=perim, centroid=cen, nbr=nbr, nrm=nrm,
+                    min_inradius=mr.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().kitrt_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MNSolver:
+    """M_N solver handle (kitrt_mn_init) bound to a Mesh."""
+
+    def __init__(self, mesh: Mesh, degree: int, quad_order: int, mode: str = "fp64",
+                 bc: str = "neumann", **opts):
+        p = Params()
+        _check(_lib().kitrt_default_params(C.byref(p)), "kitrt_default_params")
+        p.degree = degree
+        p.quad_order = quad_order
+        p.mode = MODES[mode]
+        p.bc = BCS[bc]
+        for k, v in opts.items():
+            setattr(p, k, v)
+        self.params = p
+        self.mesh = mesh
+        h = C.c_void_p()
+        _check(_lib().kitrt_mn_init(mesh.handle, C.byref(p), C.byref(h)), "kitrt_mn_init")
+        self.handle = h
+        n, Q, Qf = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(_lib().kitrt_mn_sizes(h, C.byref(n), C.byref(Q), C.byref(Qf)), "kitrt_mn_sizes")
+        self.n, self.Q, self.Qf = n.value, Q.value, Qf.value
+
+    def quadrature(self):
+        w = np.zeros(self.Qf)
+        om = np.zeros((self.Qf, 2))
+        m = np.zeros((self.Qf, self.n))
+        _check(_lib().kitrt_mn_quadrature(self.handle, _np_d(w), _np_d(om), _np_d(m)),
+               "kitrt_mn_quadrature")
+        return w, om, m
+
+    def isotropic_alpha(self, u):
+        import torch
+        alpha = torch.empty_like(u)
+        _check(_lib().kitrt_isotropic_alpha(self.handle, _dev(u, torch.float64),
+                                            _dev(alpha, torch.float64), _stream()),
+               "kitrt_isotropic_alpha")
+        return alpha
+
+    def closure(self, u, alpha, status=None, stats: bool = False, check: bool = True):
+        import torch
+        st = Stats()
+        rc = _lib().kitrt_closure(self.handle, _dev(u, torch.float64), _dev(alpha, torch.float64),
+                                  _dev(status, torch.int32), _stream(),
+                                  C.byref(st) if stats else None)
+        if check:
+            _check(rc, "kitrt_closure")
+        return (rc, st.as_dict()) if stats else rc
+
+    def ansatz(self, alpha):
+        import torch
+        psi = torch.empty((alpha.shape[0], self.Qf), dtype=torch.float64, device=alpha.device)
+        _check(_lib().kitrt_ansatz(self.handle, _dev(alpha, torch.float64), _dev(psi), _stream()),
+               "kitrt_ansatz")
+        return psi
+
+    def step(self, u, alpha, sigma_a, sigma_s, q, dt: float = 0.0, nsteps: int = 1,
+             status=None, stats: bool = False, check: bool = True):
+        import torch
+        st = Stats()
+        rc = _lib().kitrt_step(self.handle, _dev(u, torch.float64), _dev(alpha, torch.float64),
+                               _dev(sigma_a, torch.float64), _dev(sigma_s, torch.float64),
+                               _dev(q, torch.float64), float(dt), int(nsteps),
+                               _dev(status, torch.int32), _stream(),
+                               C.byref(st) if stats else None)
+        if check:
+            _check(rc, "kitrt_step")
+        return (rc, st.as_dict()) if stats else rc
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().kitrt_mn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
