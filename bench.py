@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the M_N step on one GB300 (or N independent replicas under torchrun).
+
+Workload: M_3 line source on the square [-1.5,1.5]^2, seeded jittered-point Delaunay mesh of
+224^2 points (~100k triangles), 10 moments, order-20 product quadrature (800 points, 400 after
+folding), Gaussian initial density of width 0.03 plus a 1e-4 floor, sigma_s = 1, sigma_a = 0,
+CFL 0.4, Neumann walls, Newton tolerance 1e-10.
+
+One step = one explicit M_N time step of the whole mesh: entropy closure of every cell (Newton),
+kinetic upwind flux, source and Euler update. `value` times K steps with the state resident in
+device memory; `e2e` times K steps through the same C ABI call with the state copied from pinned
+host memory before and back after every step.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M_N cell-updates/s & closures/s, mixed vs FP64 on one GB300 at stated error"
+UNIT = "cell-updates/s"
+WORKLOAD = "m3_line_source_100k"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", default="fp64", help="headline closure mode")
+    ap.add_argument("--compare", default="", help="comma list of extra modes to time")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------------------
+def make_workload():
+    from paper_2205_08417_gb300 import synth
+    spec = synth.WORKLOADS[WORKLOAD]
+    m = synth.jittered_mesh(spec["k"], spec["lo"], spec["hi"], spec["seed"])
+    cen = m.centroids()
+    n = (spec["N"] + 1) * (spec["N"] + 2) // 2
+    u0 = synth.isotropic_moments(synth.line_source_density(cen), n)
+    C = m.ncells
+    return dict(mesh=m, cen=cen, u0=u0, N=spec["N"], order=spec["order"], n=n, C=C,
+                sa=np.zeros(C), ss=np.ones(C), q=np.zeros(C))
+
+
+def oracle_sample_cells(W, size):
+    """A Morton-contiguous block of `size` cells centred on the cell nearest the pulse (the whole
+    mesh when size is None or not smaller than the mesh)."""
+    C = W["C"]
+    if size is None or size >= C:
+        return np.arange(C)
+    c0 = int(np.argmin((W["cen"] ** 2).sum(axis=1)))
+    lo = max(0, min(C - size, c0 - size // 2))
+    return np.arange(lo, lo + size)
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------------
+# oracle legs (CPU)
+# ------------------------------------------------------------------------------------------------
+def oracle_timing(W, steps: int, warmup: int, sample_cells: int):
+    """Time the CPU oracle on a bounded sample: `steps` oracle steps on a Morton-contiguous
+    submesh of `sample_cells` cells around the pulse, after `warmup` untimed steps."""
+    import oracle as O
+    cells = oracle_sample_cells(W, sample_cells)
+    m = W["mesh"]
+    G = O.Geometry(m.xy, m.tri[cells])
+    T = O.Tables(W["N"], W["order"])
+    u = np.ascontiguousarray(W["u0"][cells])
+    a = O.isotropic_alpha(T, u)
+    dt = 0.4 * float(np.min(2 * G.area / G.perim))
+    sa, ss, q = W["sa"][cells], W["ss"][cells], W["q"][cells]
+    if warmup:
+        O.mn_run(T, G, u, a, sa, ss, q, dt, warmup)
+    t0 = time.perf_counter()
+    nf, _ = O.mn_run(T, G, u, a, sa, ss, q, dt, steps)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return len(cells) * steps / el, cores, el, len(cells)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU leg
+# ------------------------------------------------------------------------------------------------
+def fp64_peak_tflops(torch):
+    """Measured FP64 throughput of cuBLAS DGEMM (4096^3, best of 5) on this GPU."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def run_mode(K, torch, W, mode, steps, warmup, e2e=True):
+    mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
+    s = K.MNSolver(mesh, W["N"], W["order"], mode=mode)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    u = d(W["u0"])
+    alpha = s.isotropic_alpha(u)
+    sa, ss, q = d(W["sa"]), d(W["ss"]), d(W["q"])
+    geo = mesh.geometry()
+    dt = 0.4 * geo["min_inradius"]
+    s.step(u, alpha, sa, ss, q, dt=dt, nsteps=warmup)
+    torch.cuda.synchronize()
+    s.profile(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rc, st = s.step(u, alpha, sa, ss, q, dt=dt, nsteps=steps, stats=True)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile_read()
+    s.profile(False)
+    out = dict(mode=mode, ms=ms, stats=st, prof=prof, dt=dt, u=u.cpu().numpy(),
+               alpha=alpha.cpu().numpy(), nbr=geo["nbr"], solver=s, mesh=mesh)
+    if e2e:
+        C, n = W["C"], W["n"]
+        host = torch.from_numpy(out["u"].copy()).pin_memory()
+        ud = torch.empty_like(u)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            ud.copy_(host, non_blocking=True)
+            s.step(ud, alpha, sa, ss, q, dt=dt, nsteps=1)
+            host.copy_(ud, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        out["e2e_ms"] = e0.elapsed_time(e1)
+        out["e2e_bytes"] = C * n * 8
+    return out
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        # the reference arm is the CPU oracle (rank 0 only)
+        if rank != 0:
+            return
+        W = make_workload()
+        import oracle as O
+        O.build()
+        cps, cores, el, ncells = oracle_timing(W, args.steps, args.warmup, None)
+        line = {"impl": "reference", "metric": METRIC, "value": cps, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "mesh_cells": W["C"], "nmom": W["n"],
+                           "quad_points": 2 * W["order"] ** 2, "mode": "oracle_fp64"},
+                "cpu_baseline": {"value": cps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"{args.steps} oracle steps after {args.warmup} "
+                                           f"untimed on the full {ncells}-cell mesh, OpenMP "
+                                           f"over cells"},
+                "e2e": {"value": cps, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2205_08417_gb300 import build, kitrt as K
+    build.build()
+    W = make_workload()
+
+    modes = [args.mode] + [m for m in args.compare.split(",") if m and m != args.mode]
+    peak = fp64_peak_tflops(torch)
+    results = {}
+    clocks = None
+    for mode in modes:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        cs = ClockSampler(local) if mode == args.mode else None
+        r = run_mode(K, torch, W, mode, args.steps, args.warmup)
+        if cs is not None:
+            clocks = cs.stop()
+        results[mode] = r
+    head = results[args.mode]
+    ms = head["ms"]
+    if world > 1:
+        t = torch.tensor([ms, head["e2e_ms"]], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    else:
+        e2e_ms = head["e2e_ms"]
+    C = W["C"]
+    value = world * C * args.steps / (ms / 1e3)
+    e2e_value = world * C * args.steps / (e2e_ms / 1e3)
+
+    n, Qf = W["n"], W["order"] ** 2
+    work = head["solver"].work()
+    fl = work["flops_per_eval"]
+    pe = head["prof"].get("closure_eval_fp64") or head["prof"].get("closure_eval_mixed")
+    achieved = pe["units"] * fl / (pe["total_ms"] / 1e3) / 1e12
+    closure_ms = sum(head["prof"][k]["total_ms"] for k in head["prof"] if k.startswith("closure"))
+    closures_per_s = C * args.steps / (closure_ms / 1e3)
+
+    errors = {}
+    if "fp64" in results:
+        ref = results["fp64"]["u"][:, 0]
+        for mname, r in results.items():
+            if mname != "fp64":
+                errors[f"{mname}_vs_fp64_u0_rel_l2"] = float(
+                    np.linalg.norm(r["u"][:, 0] - ref) / np.linalg.norm(ref))
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle as O
+        O.build()
+        cps, cores, el, ncells = oracle_timing(W, 3, 1, None)
+        cpu = {"value": cps, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"3 oracle steps after 1 untimed on the full {ncells}-cell mesh, "
+                         f"OpenMP over cells ({el:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f64+tf32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh_cells": C, "nmom": n,
+                   "quad_points": 2 * W["order"] ** 2, "quad_points_folded": Qf,
+                   "mode": args.mode, "dt": head["dt"], "tau": 1e-10, "parallelism": f"replicas{world}",
+                   "l2": "working set > L2: FP64 psi (C x Q' x 8 B = "
+                         f"{C * (Qf + 31) // 32 * 32 * 8 / 1e6:.0f} MB) written and re-read every step"},
+        "closures_per_s": closures_per_s,
+        "evaluations_per_cell_step": head["stats"]["evaluations"] / (C * args.steps),
+        "roofline": {"kernel": "closure_eval_fp64" if "closure_eval_fp64" in head["prof"] else "closure_eval_mixed",
+                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "measured cuBLAS DGEMM 4096^3 in this run (FP64 pipe)",
+                     "flops_per_cell_eval": fl, "exps_per_cell_eval": work["exps_per_eval"],
+                     "gaunt_nnz": work["gaunt_nnz"], "cell_evals": pe["units"],
+                     "launches": pe["launches"], "avg_launch_ms": pe["total_ms"] / pe["launches"]},
+        "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
+                        "share": v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in head["prof"].values()))}
+                    for k, v in head["prof"].items()},
+        "modes": {m: {"cell_updates_per_s": C * args.steps / (r["ms"] / 1e3),
+                      "ms_per_step": r["ms"] / args.steps,
+                      "evaluations_per_cell_step": r["stats"]["evaluations"] / (C * args.steps)}
+                  for m, r in results.items()},
+        "error": errors,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["e2e_bytes"],
+                "d2h_bytes_per_step": head["e2e_bytes"]},
+        "gpu_launches": int(head["stats"]["launches"]),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

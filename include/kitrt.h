@@ -69,7 +69,7 @@ typedef struct kitrt_mesh kitrt_mesh;
 typedef struct kitrt_mn kitrt_mn;
 
 typedef struct {
-    int32_t degree;        /* N >= 0; nmom = (N+1)(N+2)/2; N <= 7 */
+    int32_t degree;        /* 1 <= N <= 5; nmom = (N+1)(N+2)/2 */
     int32_t quad_order;    /* Gauss points in mu (>= N+1); Q = 2 order^2 */
     int32_t mode;          /* KITRT_FP64 / KITRT_MIXED_TF32 / KITRT_MIXED_BF16 / KITRT_LEARNED */
     int32_t bc;            /* KITRT_BC_NEUMANN / KITRT_BC_VACUUM */
@@ -91,7 +91,17 @@ typedef struct {
     int32_t failed;        /* cells whose last closure ended with a non-zero status */
     int64_t fallbacks;     /* KITRT_LEARNED: cells that needed Newton after the MLP */
     double dt;             /* time step used */
+    int64_t launches;      /* CUDA kernels the library launched in this call */
 } kitrt_stats;
+
+/* Per-kernel-kind trace record (see kitrt_profile_enable). `units` counts what one kind
+ * processes: cell evaluations of the dual for the closure sweeps, cells for the other kernels. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    int64_t units;
+    double total_ms;       /* device time between CUDA events recorded around each launch */
+} kitrt_profile_entry;
 
 /* Human-readable name of a status code (static string). */
 const char *kitrt_status_string(int32_t code);
@@ -127,6 +137,17 @@ int32_t kitrt_mn_destroy(kitrt_mn *mn);
 
 /* Sizes: moments n, quadrature points Q of the full rule and Q' after folding. */
 int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_t *nquad_folded);
+
+/* Work accounting of one cell evaluation of the dual (one quadrature pass): moments n, degree-2N
+ * moments n2, folded points Q', non-zero Gaunt coefficients, and the algorithmic FP64 flops of
+ * the pass without exp: 2nQ' (exponents) + Q' (weights) + 2 n2 Q' (moment sums) + 2 nnz
+ * (Hessian) + n^3/3 + 2n^2 (Cholesky and solves). */
+typedef struct {
+    int32_t nmom, nmom2, nquad_folded, gaunt_nnz;
+    double flops_per_eval;
+    double exps_per_eval;
+} kitrt_work;
+int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out);
 
 /* Copy the folded quadrature to host arrays (any may be NULL): weights [Q'], 2D directions
  * [Q' x 2], basis values [Q' x nmom]. */
@@ -167,6 +188,15 @@ int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *strea
 int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a,
                    const double *sigma_s, const double *q, double dt, int32_t nsteps,
                    int32_t *status, void *stream, kitrt_stats *stats);
+
+/* Tracing: on != 0 resets the trace and records a pair of CUDA events on the launching stream
+ * around every kernel the solver launches from then on; on == 0 stops recording. */
+int32_t kitrt_profile_enable(kitrt_mn *mn, int32_t on);
+
+/* Read the trace (synchronises with the recorded events): up to max_entries records, one per
+ * kernel kind that ran, into `out` (host); *n_entries receives the number written. */
+int32_t kitrt_profile_read(kitrt_mn *mn, kitrt_profile_entry *out, int32_t max_entries,
+                           int32_t *n_entries);
 
 #ifdef __cplusplus
 }

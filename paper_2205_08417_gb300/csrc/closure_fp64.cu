@@ -213,6 +213,7 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
             const int ev = S.evals[cell] + 1;
             S.evals[cell] = ev;
             atomicMax(&S.cnt[4], ev);
+            atomicAdd(&S.cnt[6], 1);
         }
 
         bool accept;
@@ -387,27 +388,30 @@ int launch_ansatz(const Tables &T, int C, const double *alpha, double *psi, cuda
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
-int launch_begin(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                  const double *u, const double *alpha_in, int first, NewtonParams np,
                  cudaStream_t s)
 {
     const int grid = grid_for(mn, C, 8);
+    LaunchScope ls(mn, PK_BEGIN, s, C);
     KITRT_DISPATCH_N(mn->N, begin_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, S, u, alpha_in, first, np, C));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
-int launch_eval_fp64(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s)
 {
     const int grid = grid_for(mn, C, 4);
+    LaunchScope ls(mn, PK_EVAL, s, 0);
     KITRT_DISPATCH_N(mn->N, eval_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
-int launch_finish(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+int launch_finish(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                   double *alpha_out, double *psi, float *psi32, int polish, cudaStream_t s)
 {
     const int grid = grid_for(mn, C, 8);
+    LaunchScope ls(mn, PK_FINISH, s, C);
     KITRT_DISPATCH_N(mn->N, finish_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, S, alpha_out, psi, psi32, polish, C));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }

@@ -78,7 +78,7 @@ flux_update_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restr
 
 }  // namespace
 
-int launch_flux_update(const kitrt_mn *mn, const Tables &T, int C, const double *psi,
+int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
                        const float *psi32, double *u, const double *sa, const double *ss,
                        const double *q, double dt, int bc, cudaStream_t s)
 {
@@ -86,6 +86,7 @@ int launch_flux_update(const kitrt_mn *mn, const Tables &T, int C, const double 
     int need = (C + kWarps - 1) / kWarps;
     int cap = mn->nsm * 8;
     int grid = need < cap ? (need > 0 ? need : 1) : cap;
+    LaunchScope ls(mn, PK_FLUX, s, C);
 #define FLUX_CASE(NN)                                                                          \
     case NN:                                                                                   \
         if (psi)                                                                               \

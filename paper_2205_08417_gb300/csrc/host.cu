@@ -144,6 +144,32 @@ int dev_alloc(kitrt_mn *mn, T **dst, size_t count)
 
 }  // namespace
 
+LaunchScope::LaunchScope(kitrt_mn *m, int k, cudaStream_t st, int64_t units) : mn(m), kind(k), s(st)
+{
+    ++mn->launch_count;
+    if (!mn->prof_on) return;
+    mn->prof_launches[k] += 1;
+    mn->prof_units[k] += units;
+    if (mn->prof_used >= 65536) return;
+    if (mn->prof_used == mn->prof_recs.size()) {
+        ProfRec r{};
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+        mn->prof_recs.push_back(r);
+    }
+    rec = &mn->prof_recs[mn->prof_used++];
+    rec->kind = k;
+    cudaEventRecord(rec->a, s);
+}
+
+LaunchScope::~LaunchScope()
+{
+    if (rec) cudaEventRecord(rec->b, s);
+}
+
+static const char *kProfNames[PK_COUNT] = {"closure_begin", "closure_eval_fp64", "closure_finish",
+                                           "flux_update", "closure_eval_mixed", "mlp",
+                                           "adjoint", "other"};
+
 Tables kitrt_mn::tables() const
 {
     Tables T;
@@ -315,6 +341,10 @@ int32_t kitrt_mesh_geometry(const kitrt_mesh *m, int32_t *ncells, double *min_in
 int32_t kitrt_mn_destroy(kitrt_mn *mn)
 {
     if (!mn) return KITRT_EINVAL;
+    for (ProfRec &r : mn->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
     for (void *p : mn->allocs) cudaFree(p);
     if (mn->h_cnt) cudaFreeHost(mn->h_cnt);
     delete mn;
@@ -402,6 +432,7 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
         }
     }
     gstart[mn->npairs] = (int32_t)gidx.size();
+    mn->gaunt_nnz = (int)gidx.size();
     std::vector<float> Mt32(Mt.begin(), Mt.end()), w32(w.begin(), w.end());
     TRY(dev_upload(mn, &mn->d_Mt, Mt));
     TRY(dev_upload(mn, &mn->d_w, w));
@@ -449,6 +480,19 @@ int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_
     if (nmom) *nmom = mn->n;
     if (nquad) *nquad = mn->Q;
     if (nquad_folded) *nquad_folded = mn->Qf;
+    return KITRT_OK;
+}
+
+int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out)
+{
+    if (!mn || !out) return KITRT_EINVAL;
+    const double n = mn->n, n2 = mn->n2, Qf = mn->Qf;
+    out->nmom = mn->n;
+    out->nmom2 = mn->n2;
+    out->nquad_folded = mn->Qf;
+    out->gaunt_nnz = mn->gaunt_nnz;
+    out->flops_per_eval = 2 * n * Qf + Qf + 2 * n2 * Qf + 2.0 * mn->gaunt_nnz + n * n * n / 3 + 2 * n * n;
+    out->exps_per_eval = Qf;
     return KITRT_OK;
 }
 
@@ -504,8 +548,10 @@ static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, in
         if (active == 0) break;
         if (k >= max_launch) return KITRT_ETIMEOUT;
     }
+    if (mn->prof_on) mn->prof_units[PK_EVAL] += mn->h_cnt[6];
     if (stats) {
         stats->closures += C;
+        stats->evaluations += mn->h_cnt[6];
         stats->max_evals = std::max(stats->max_evals, mn->h_cnt[4]);
         stats->failed = mn->h_cnt[3];
     }
@@ -527,13 +573,17 @@ int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *sta
     if (!mn || !u || !alpha) return KITRT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (stats) memset(stats, 0, sizeof(*stats));
+    const int64_t launches0 = mn->launch_count;
     int rc = run_closure(mn, u, alpha, 1, s, stats);
     int rc2 = launch_finish(mn, mn->tables(), mn->st, mn->mesh->C, alpha, nullptr, nullptr,
                             mn->p.polish, s);
     if (status)
         CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * mn->mesh->C,
                                 cudaMemcpyDeviceToDevice, s));
-    if (stats) CUDA_OK(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->launches = mn->launch_count - launches0;
+        CUDA_OK(cudaStreamSynchronize(s));
+    }
     return rc ? rc : rc2;
 }
 
@@ -554,6 +604,7 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
         memset(stats, 0, sizeof(*stats));
         stats->dt = dt;
     }
+    const int64_t launches0 = mn->launch_count;
     const int C = mn->mesh->C;
     const Tables T = mn->tables();
     int rc = KITRT_OK;
@@ -568,8 +619,48 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
     if (status)
         CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * C,
                                 cudaMemcpyDeviceToDevice, s));
-    if (stats) CUDA_OK(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->launches = mn->launch_count - launches0;
+        CUDA_OK(cudaStreamSynchronize(s));
+    }
     return rc;
+}
+
+int32_t kitrt_profile_enable(kitrt_mn *mn, int32_t on)
+{
+    if (!mn) return KITRT_EINVAL;
+    if (on) {
+        mn->prof_used = 0;
+        for (int k = 0; k < PK_COUNT; ++k) mn->prof_launches[k] = mn->prof_units[k] = 0;
+    }
+    mn->prof_on = on != 0;
+    return KITRT_OK;
+}
+
+int32_t kitrt_profile_read(kitrt_mn *mn, kitrt_profile_entry *out, int32_t max_entries,
+                           int32_t *n_entries)
+{
+    if (!mn || (!out && max_entries > 0)) return KITRT_EINVAL;
+    double ms[PK_COUNT] = {};
+    for (size_t i = 0; i < mn->prof_used; ++i) {
+        ProfRec &r = mn->prof_recs[i];
+        CUDA_OK(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        CUDA_OK(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.kind] += t;
+    }
+    int cnt = 0;
+    for (int k = 0; k < PK_COUNT && cnt < max_entries; ++k) {
+        if (mn->prof_launches[k] == 0) continue;
+        kitrt_profile_entry &e = out[cnt++];
+        memset(&e, 0, sizeof(e));
+        strncpy(e.name, kProfNames[k], sizeof(e.name) - 1);
+        e.launches = mn->prof_launches[k];
+        e.units = mn->prof_units[k];
+        e.total_ms = ms[k];
+    }
+    if (n_entries) *n_entries = cnt;
+    return KITRT_OK;
 }
 
 }  // extern "C"

@@ -65,11 +65,21 @@ struct NewtonParams {
     int max_iter, max_halvings, polish;
 };
 
+// Kernel kinds recorded by the tracer.
+enum ProfKind : int { PK_BEGIN = 0, PK_EVAL = 1, PK_FINISH = 2, PK_FLUX = 3, PK_EVAL_MIXED = 4,
+                      PK_MLP = 5, PK_ADJOINT = 6, PK_OTHER = 7, PK_COUNT = 8 };
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
 struct kitrt_mn {
     const kitrt_mesh *mesh = nullptr;
     kitrt_mn_params p{};
     int N = 0, n = 0, n2 = 0, npairs = 0, Q = 0, Qf = 0, Qp = 0;
     int nsm = 0;
+    int gaunt_nnz = 0;
     std::vector<double> h_w, h_ox, h_oy, h_M;  // folded tables (host copies; M is [Qf x n])
     // device tables
     double *d_Mt = nullptr, *d_w = nullptr, *d_wox = nullptr, *d_woy = nullptr;
@@ -82,19 +92,35 @@ struct kitrt_mn {
     float *d_psi32 = nullptr;  // [C x Qp] FP32 ansatz (mixed modes)
     int32_t *h_cnt = nullptr;  // pinned copy of st.cnt
     std::vector<void *> allocs;
+    // tracing
+    bool prof_on = false;
+    std::vector<ProfRec> prof_recs;
+    size_t prof_used = 0;
+    int64_t prof_launches[PK_COUNT] = {}, prof_units[PK_COUNT] = {};
+    int64_t launch_count = 0;  // kernels launched (all calls)
     Tables tables() const;
+};
+
+// Records CUDA events around one kernel launch when tracing is on, and counts the launch.
+struct LaunchScope {
+    kitrt_mn *mn;
+    int kind;
+    cudaStream_t s;
+    ProfRec *rec = nullptr;
+    LaunchScope(kitrt_mn *m, int k, cudaStream_t st, int64_t units);
+    ~LaunchScope();
 };
 
 // Kernel launchers (closure_fp64.cu, flux.cu).
 int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cudaStream_t s);
-int launch_begin(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                  const double *u, const double *alpha_in, int first, NewtonParams np,
                  cudaStream_t s);
-int launch_eval_fp64(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s);
-int launch_finish(const kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
+int launch_finish(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                   double *alpha_out, double *psi, float *psi32, int polish, cudaStream_t s);
 int launch_ansatz(const Tables &T, int C, const double *alpha, double *psi, cudaStream_t s);
-int launch_flux_update(const kitrt_mn *mn, const Tables &T, int C, const double *psi,
+int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
                        const float *psi32, double *u, const double *sa, const double *ss,
                        const double *q, double dt, int bc, cudaStream_t s);

@@ -36,10 +36,22 @@ class Params(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("closures", C.c_int64), ("evaluations", C.c_int64), ("max_evals", C.c_int32),
-                ("failed", C.c_int32), ("fallbacks", C.c_int64), ("dt", C.c_double)]
+                ("failed", C.c_int32), ("fallbacks", C.c_int64), ("dt", C.c_double),
+                ("launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Work(C.Structure):
+    _fields_ = [("nmom", C.c_int32), ("nmom2", C.c_int32), ("nquad_folded", C.c_int32),
+                ("gaunt_nnz", C.c_int32), ("flops_per_eval", C.c_double),
+                ("exps_per_eval", C.c_double)]
+
+
+class ProfileEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("units", C.c_int64),
+                ("total_ms", C.c_double)]
 
 
 _LIB = None
@@ -57,12 +69,15 @@ SIGNATURES = {
     "kitrt_mn_init": (C.c_int32, [_vp, C.POINTER(Params), C.POINTER(_vp)]),
     "kitrt_mn_destroy": (C.c_int32, [_vp]),
     "kitrt_mn_sizes": (C.c_int32, [_vp, _ip, _ip, _ip]),
+    "kitrt_mn_work": (C.c_int32, [_vp, C.POINTER(Work)]),
     "kitrt_mn_quadrature": (C.c_int32, [_vp, _dp, _dp, _dp]),
     "kitrt_isotropic_alpha": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_closure": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Stats)]),
     "kitrt_ansatz": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_step": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int32, _vp, _vp,
                                C.POINTER(Stats)]),
+    "kitrt_profile_enable": (C.c_int32, [_vp, C.c_int32]),
+    "kitrt_profile_read": (C.c_int32, [_vp, C.POINTER(ProfileEntry), C.c_int32, _ip]),
 }
 
 
@@ -174,6 +189,11 @@ class MNSolver:
         _check(_lib().kitrt_mn_sizes(h, C.byref(n), C.byref(Q), C.byref(Qf)), "kitrt_mn_sizes")
         self.n, self.Q, self.Qf = n.value, Q.value, Qf.value
 
+    def work(self):
+        w = Work()
+        _check(_lib().kitrt_mn_work(self.handle, C.byref(w)), "kitrt_mn_work")
+        return {k: getattr(w, k) for k, _ in w._fields_}
+
     def quadrature(self):
         w = np.zeros(self.Qf)
         om = np.zeros((self.Qf, 2))
@@ -219,6 +239,16 @@ class MNSolver:
         if check:
             _check(rc, "kitrt_step")
         return (rc, st.as_dict()) if stats else rc
+
+    def profile(self, on: bool = True):
+        _check(_lib().kitrt_profile_enable(self.handle, int(on)), "kitrt_profile_enable")
+
+    def profile_read(self):
+        arr = (ProfileEntry * 16)()
+        cnt = C.c_int32()
+        _check(_lib().kitrt_profile_read(self.handle, arr, 16, C.byref(cnt)), "kitrt_profile_read")
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, units=arr[i].units,
+                                           total_ms=arr[i].total_ms) for i in range(cnt.value)}
 
     def close(self):
         if getattr(self, "handle", None):
