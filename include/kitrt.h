@@ -46,7 +46,8 @@ typedef enum {
     KITRT_ELINESEARCH = 5,     /* Armijo backtracking exhausted max_halvings */
     KITRT_ECUDA = 6,           /* a CUDA runtime call failed */
     KITRT_ENOMEM = 7,          /* device allocation failed */
-    KITRT_ETIMEOUT = 8         /* a bounded device wait expired */
+    KITRT_ETIMEOUT = 8,        /* a bounded device wait expired */
+    KITRT_ESCRATCH = 9         /* batch larger than the fixed scratch of kitrt_closure_noalloc */
 } kitrt_status;
 
 /* Closure arithmetic. */
@@ -188,6 +189,26 @@ int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *strea
 int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a,
                    const double *sigma_s, const double *q, double dt, int32_t nsteps,
                    int32_t *status, void *stream, kitrt_stats *stats);
+
+/* Entropy closure of a batch of moment vectors without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot let the library allocate device
+ * memory at call time (a framework whose pool allocator owns the free memory, code running while
+ * a stream is captured, a service that must not grow after start-up) and whose batch is not the
+ * solver's mesh. It runs the same Newton iteration as kitrt_closure with the solver's tables and
+ * parameters, but keeps its per-cell Newton state in one static device array of 8 MiB that every
+ * GPU loading the library holds until the process exits.
+ *   u      device [ncells x nmom], read only; alpha device [ncells x nmom], warm start in,
+ *          solution out; status device [ncells] or NULL.
+ *   ncells may not exceed floor(8 MiB / per-cell bytes), where a cell needs
+ *          8 (3 nmom + 4 + nmom (nmom+1)/2) + 28 bytes plus 256-byte padding of 16 arrays
+ *          (about 11,300 cells for N = 3, 3,400 for N = 5); larger batches return
+ *          KITRT_ESCRATCH before touching any memory.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. Every call shares the
+ * array and leaves its contents behind; calls that overlap on the GPU (other streams or host
+ * threads) race on it. Synchronises with `stream` like kitrt_closure. */
+int32_t kitrt_closure_noalloc(const kitrt_mn *mn, const double *u, double *alpha,
+                              int32_t *status, int32_t ncells, void *stream);
 
 /* Tracing: on != 0 resets the trace and records a pair of CUDA events on the launching stream
  * around every kernel the solver launches from then on; on == 0 stops recording. */

@@ -205,6 +205,7 @@ const char *kitrt_status_string(int32_t code)
     case KITRT_ECUDA: return "CUDA runtime error";
     case KITRT_ENOMEM: return "device allocation failed";
     case KITRT_ETIMEOUT: return "bounded device wait expired";
+    case KITRT_ESCRATCH: return "batch exceeds the fixed scratch of kitrt_closure_noalloc";
     default: return "unknown status";
     }
 }

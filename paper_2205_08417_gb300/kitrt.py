@@ -16,7 +16,7 @@ from . import build as _build
 
 KITRT_OK = 0
 STATUS_NAMES = {0: "ok", 1: "EINVAL", 2: "ENOTREALIZABLE", 3: "ENOCONVERGE", 4: "ECHOL",
-                5: "ELINESEARCH", 6: "ECUDA", 7: "ENOMEM", 8: "ETIMEOUT"}
+                5: "ELINESEARCH", 6: "ECUDA", 7: "ENOMEM", 8: "ETIMEOUT", 9: "ESCRATCH"}
 MODES = {"fp64": 0, "mixed_tf32": 1, "mixed_bf16": 2, "learned": 3}
 BCS = {"neumann": 0, "vacuum": 1}
 
@@ -76,6 +76,7 @@ SIGNATURES = {
     "kitrt_ansatz": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_step": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int32, _vp, _vp,
                                C.POINTER(Stats)]),
+    "kitrt_closure_noalloc": (C.c_int32, [_vp, _vp, _vp, _vp, C.c_int32, _vp]),
     "kitrt_profile_enable": (C.c_int32, [_vp, C.c_int32]),
     "kitrt_profile_read": (C.c_int32, [_vp, C.POINTER(ProfileEntry), C.c_int32, _ip]),
 }
@@ -219,6 +220,17 @@ class MNSolver:
         if check:
             _check(rc, "kitrt_closure")
         return (rc, st.as_dict()) if stats else rc
+
+    def closure_noalloc(self, u, alpha, status=None, check: bool = True):
+        """Closure of a batch (any number of rows up to the fixed scratch limit) through the
+        allocation-free entry point."""
+        import torch
+        rc = _lib().kitrt_closure_noalloc(self.handle, _dev(u, torch.float64),
+                                          _dev(alpha, torch.float64), _dev(status, torch.int32),
+                                          int(u.shape[0]), _stream())
+        if check:
+            _check(rc, "kitrt_closure_noalloc")
+        return rc
 
     def ansatz(self, alpha):
         import torch
