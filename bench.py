@@ -44,15 +44,20 @@ def parse_args():
     ap.add_argument("--mode", default="fp64", help="headline closure mode")
     ap.add_argument("--compare", default="", help="comma list of extra modes to time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="synth.WORKLOADS key (the default is the benchmarked configuration)")
+    ap.add_argument("--t-start", type=float, default=0.25,
+                    help="simulated time reached by untimed set-up steps before warm-up")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------------------------------------
 # workload
 # ------------------------------------------------------------------------------------------------
-def make_workload():
+def make_workload(name=WORKLOAD):
     from paper_2205_08417_gb300 import synth
-    spec = synth.WORKLOADS[WORKLOAD]
+    spec = synth.WORKLOADS[name]
     m = synth.jittered_mesh(spec["k"], spec["lo"], spec["hi"], spec["seed"])
     cen = m.centroids()
     n = (spec["N"] + 1) * (spec["N"] + 2) // 2
@@ -125,7 +130,9 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 def oracle_timing(W, steps: int, warmup: int, sample_cells: int):
     """Time the CPU oracle on a bounded sample: `steps` oracle steps on a Morton-contiguous
-    submesh of `sample_cells` cells around the pulse, after `warmup` untimed steps."""
+    submesh of `sample_cells` cells around the pulse (or the whole mesh), after `warmup` untimed
+    steps from the initial state. The oracle evaluates the dual at least once for every cell in
+    every step, so its cost per cell barely depends on how far the pulse has spread."""
     import oracle as O
     cells = oracle_sample_cells(W, sample_cells)
     m = W["mesh"]
@@ -165,7 +172,7 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-def run_mode(K, torch, W, mode, steps, warmup, e2e=True):
+def run_mode(K, torch, W, mode, steps, warmup, t_start, e2e=True):
     mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
     s = K.MNSolver(mesh, W["N"], W["order"], mode=mode)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -174,6 +181,9 @@ def run_mode(K, torch, W, mode, steps, warmup, e2e=True):
     sa, ss, q = d(W["sa"]), d(W["ss"]), d(W["q"])
     geo = mesh.geometry()
     dt = 0.4 * geo["min_inradius"]
+    setup = int(round(t_start / dt))
+    if setup:
+        s.step(u, alpha, sa, ss, q, dt=dt, nsteps=setup)
     s.step(u, alpha, sa, ss, q, dt=dt, nsteps=warmup)
     torch.cuda.synchronize()
     s.profile(True)
@@ -187,7 +197,7 @@ def run_mode(K, torch, W, mode, steps, warmup, e2e=True):
     ms = e0.elapsed_time(e1)
     prof = s.profile_read()
     s.profile(False)
-    out = dict(mode=mode, ms=ms, stats=st, prof=prof, dt=dt, u=u.cpu().numpy(),
+    out = dict(mode=mode, ms=ms, stats=st, prof=prof, dt=dt, setup=setup, u=u.cpu().numpy(),
                alpha=alpha.cpu().numpy(), nbr=geo["nbr"], solver=s, mesh=mesh)
     if e2e:
         C, n = W["C"], W["n"]
@@ -216,7 +226,7 @@ def main():
         # the reference arm is the CPU oracle (rank 0 only)
         if rank != 0:
             return
-        W = make_workload()
+        W = make_workload(args.workload)
         import oracle as O
         O.build()
         cps, cores, el, ncells = oracle_timing(W, args.steps, args.warmup, None)
@@ -224,7 +234,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "mesh_cells": W["C"], "nmom": W["n"],
+                "config": {"workload": args.workload, "mesh_cells": W["C"], "nmom": W["n"],
                            "quad_points": 2 * W["order"] ** 2, "mode": "oracle_fp64"},
                 "cpu_baseline": {"value": cps, "unit": UNIT, "cores": cores, "kind": "oracle",
                                  "sample": f"{args.steps} oracle steps after {args.warmup} "
@@ -244,7 +254,7 @@ def main():
         torch.cuda.set_device(0)
     from paper_2205_08417_gb300 import build, kitrt as K
     build.build()
-    W = make_workload()
+    W = make_workload(args.workload)
 
     modes = [args.mode] + [m for m in args.compare.split(",") if m and m != args.mode]
     peak = fp64_peak_tflops(torch)
@@ -255,7 +265,7 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
         cs = ClockSampler(local) if mode == args.mode else None
-        r = run_mode(K, torch, W, mode, args.steps, args.warmup)
+        r = run_mode(K, torch, W, mode, args.steps, args.warmup, args.t_start, e2e=not args.no_e2e)
         if cs is not None:
             clocks = cs.stop()
         results[mode] = r
@@ -266,12 +276,12 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms, e2e_ms = float(t[0]), float(t[1])
     else:
-        e2e_ms = head["e2e_ms"]
+        e2e_ms = head.get("e2e_ms", float("nan"))
     C = W["C"]
     value = world * C * args.steps / (ms / 1e3)
     e2e_value = world * C * args.steps / (e2e_ms / 1e3)
 
-    n, Qf = W["n"], W["order"] ** 2
+    n, Qf = W["n"], W["order"] ** 2  # folded points Q' = Q/2 = order^2
     work = head["solver"].work()
     fl = work["flops_per_eval"]
     pe = head["prof"].get("closure_eval_fp64") or head["prof"].get("closure_eval_mixed")
@@ -301,9 +311,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f64+tf32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "mesh_cells": C, "nmom": n,
+        "config": {"workload": args.workload, "mesh_cells": C, "nmom": n,
                    "quad_points": 2 * W["order"] ** 2, "quad_points_folded": Qf,
                    "mode": args.mode, "dt": head["dt"], "tau": 1e-10, "parallelism": f"replicas{world}",
+                   "t_start": args.t_start, "setup_steps": head["setup"],
                    "l2": "working set > L2: FP64 psi (C x Q' x 8 B = "
                          f"{C * (Qf + 31) // 32 * 32 * 8 / 1e6:.0f} MB) written and re-read every step"},
         "closures_per_s": closures_per_s,
@@ -323,8 +334,9 @@ def main():
                       "evaluations_per_cell_step": r["stats"]["evaluations"] / (C * args.steps)}
                   for m, r in results.items()},
         "error": errors,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["e2e_bytes"],
-                "d2h_bytes_per_step": head["e2e_bytes"]},
+        "e2e": None if args.no_e2e else {
+            "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["e2e_bytes"],
+            "d2h_bytes_per_step": head["e2e_bytes"]},
         "gpu_launches": int(head["stats"]["launches"]),
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -169,6 +169,12 @@ int32_t kitrt_isotropic_alpha(kitrt_mn *mn, const double *u, double *alpha, void
 int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
                       void *stream, kitrt_stats *stats);
 
+/* Hessian of the dual, H = <m m^T exp(alpha.m)>, of every cell at the given alpha, computed the
+ * way the solver's closure computes it (FP64, or with the degree N+1..2N moments on tensor
+ * cores in the mixed modes). alpha device [C x n]; H device [C x n x n] row-major, symmetric.
+ * The first call allocates a [C x (2N+1)(2N+2)/2] moments buffer owned by the solver. */
+int32_t kitrt_hessian(kitrt_mn *mn, const double *alpha, double *H, void *stream);
+
 /* The closed ansatz at the folded quadrature points: psi [C x Q'] FP64 device,
  * psi_cq = exp(alpha_c . m_q). */
 int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *stream);

@@ -14,85 +14,12 @@
 #include <math.h>
 
 #include "kitrt_internal.cuh"
+#include "newton_common.cuh"
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using namespace kitrt_dev;
 constexpr int kWarps = 8;  // warps per block
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ void push(int32_t *list, int32_t *cnt, int cell, int lane)
-{
-    if (lane == 0) {
-        int pos = atomicAdd(cnt, 1);
-        list[pos] = cell;
-    }
-}
-
-__device__ __forceinline__ void fail(const NewtonState &S, int cell, int code, int lane)
-{
-    if (lane == 0) {
-        S.status[cell] = code;
-        S.phase[cell] = PH_DONE;
-        atomicAdd(&S.cnt[3], 1);
-    }
-}
-
-// Packed lower-triangle index of (a, b), b <= a.
-__device__ __forceinline__ int tri_idx(int a, int b) { return a * (a + 1) / 2 + b; }
-
-// Warp Cholesky of the n x n matrix in sH (row-major); on success the lower triangle holds L.
-template <int n>
-__device__ bool warp_cholesky(double *sH, int lane)
-{
-    for (int j = 0; j < n; ++j) {
-        const double djj = sH[j * n + j];
-        if (!(djj > 0.0)) return false;  // warp-uniform: every lane read the same value
-        const double ljj = sqrt(djj);
-        const double rinv = 1.0 / ljj;
-        __syncwarp();
-        if (lane > j && lane < n) sH[lane * n + j] *= rinv;
-        if (lane == j) sH[j * n + j] = ljj;
-        __syncwarp();
-        if (lane > j && lane < n) {
-            const double lij = sH[lane * n + j];
-            for (int k = j + 1; k <= lane; ++k) sH[lane * n + k] = fma(-lij, sH[k * n + j], sH[lane * n + k]);
-        }
-        __syncwarp();
-    }
-    return true;
-}
-
-// Solve L L^T x = b with lane a holding b_a; returns x_a in lane a.
-template <int n>
-__device__ double warp_chol_solve(const double *sH, double b, int lane)
-{
-    double y = b;
-    for (int j = 0; j < n; ++j) {
-        const double yj = __shfl_sync(kFull, y, j) / sH[j * n + j];
-        if (lane == j) y = yj;
-        if (lane > j && lane < n) y = fma(-sH[lane * n + j], yj, y);
-    }
-    for (int j = n - 1; j >= 0; --j) {
-        const double xj = __shfl_sync(kFull, y, j) / sH[j * n + j];
-        if (lane == j) y = xj;
-        if (lane < j) y = fma(-sH[j * n + lane], xj, y);
-    }
-    return lane < n ? y : 0.0;
-}
-
-template <int NN>
-struct Dims {
-    static constexpr int n = (NN + 1) * (NN + 2) / 2;
-    static constexpr int n2 = (2 * NN + 1) * (2 * NN + 2) / 2;
-    static constexpr int npairs = n * (n + 1) / 2;
-};
 
 // ---------------------------------------------------------------------------------------------
 // begin: start a closure. first != 0: every cell starts from alpha_in with an evaluation.
@@ -116,6 +43,8 @@ begin_kernel(Tables T, NewtonState S, const double *__restrict__ u, const double
             S.halv[cell] = 0;
             S.evals[cell] = 0;
             S.status[cell] = 0;
+            if (S.h64) S.h64[cell] = 0;
+            if (S.gnorm) S.gnorm[cell] = INFINITY;
         }
         if (first) {
             if (lane < n) S.alpha[off + lane] = alpha_in[off + lane];
@@ -126,6 +55,14 @@ begin_kernel(Tables T, NewtonState S, const double *__restrict__ u, const double
         const double ua = lane < n ? u[off + lane] : 0.0;
         const double al = lane < n ? S.alpha[off + lane] : 0.0;
         const double g = lane < n ? S.U[off + lane] - ua : 0.0;
+        const double gn2 = warp_sum(g * g), un2 = warp_sum(ua * ua);
+        if (gn2 <= kRoundoff2 * un2) {
+            // residual already at round-off: no Newton step and no polish (it would move alpha
+            // by less than its own rounding)
+            if (lane < n) S.dir[off + lane] = 0.0;
+            if (lane == 0) S.phase[cell] = PH_DONE;
+            continue;
+        }
         for (int a = lane; a < n; a += 32)
             for (int b = 0; b <= a; ++b) {
                 const double v = S.L[(size_t)cell * npairs + tri_idx(a, b)];
@@ -134,7 +71,6 @@ begin_kernel(Tables T, NewtonState S, const double *__restrict__ u, const double
         __syncwarp();
         const double d = warp_chol_solve<n>(H, -g, lane);
         __syncwarp();
-        const double gn2 = warp_sum(g * g), un2 = warp_sum(ua * ua);
         if (lane < n) S.dir[off + lane] = d;
         if (sqrt(gn2) <= np.tau * sqrt(un2)) {
             if (lane == 0) S.phase[cell] = PH_DONE;
@@ -142,6 +78,7 @@ begin_kernel(Tables T, NewtonState S, const double *__restrict__ u, const double
         }
         const double au = warp_sum(al * ua), gd = warp_sum(g * d);
         if (lane == 0) {
+            if (S.gnorm) S.gnorm[cell] = sqrt(gn2);
             const double fs = S.fsum[cell];
             S.f0[cell] = fs - au;
             S.gd[cell] = gd;
@@ -157,11 +94,11 @@ begin_kernel(Tables T, NewtonState S, const double *__restrict__ u, const double
 // Armijo decision, and on acceptance the Hessian, its Cholesky factor, the convergence test and
 // the next Newton direction.
 // ---------------------------------------------------------------------------------------------
-template <int NN>
+template <int NN, bool FILTER>
 __global__ void __launch_bounds__(kWarps * 32)
 eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np)
 {
-    constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2, npairs = Dims<NN>::npairs;
+    constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2;
     __shared__ double sH[kWarps][n * n];
     __shared__ double sV[kWarps][n2];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -169,7 +106,9 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
     int32_t *list_out = S.list[(k + 1) & 1];
     const int cnt_in = S.cnt[k % 3];
     int32_t *cnt_out = &S.cnt[(k + 1) % 3];
-    if (blockIdx.x == 0 && threadIdx.x == 0) S.cnt[(k + 2) % 3] = 0;
+    // FILTER: the FP64 companion of the mixed sweep; it only takes cells flagged for an FP64
+    // Hessian and leaves the counter bookkeeping to the mixed kernel
+    if (!FILTER && blockIdx.x == 0 && threadIdx.x == 0) S.cnt[(k + 2) % 3] = 0;
     double *H = sH[wib];
     double *Vs = sV[wib];
     const int Qp = T.Qp;
@@ -178,6 +117,7 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
 
     for (int it = blockIdx.x * kWarps + wib; it < cnt_in; it += gridDim.x * kWarps) {
         const int cell = list_in[it];
+        if (FILTER && S.h64[cell] == 0) continue;
         const size_t off = (size_t)cell * n;
         const int ph = S.phase[cell];
         const double ua = lane < n ? u[off + lane] : 0.0;
@@ -200,101 +140,15 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
 #pragma unroll
             for (int c = 0; c < n2; ++c) V[c] = fma(e, Mt[c * Qp + q], V[c]);
         }
-        bool finite = true;
 #pragma unroll
-        for (int c = 0; c < n2; ++c) {
-            V[c] = warp_sum(V[c]);
-            finite = finite && isfinite(V[c]);
-        }
-        const double fs = V[0] / T.m0;
-        const double au = warp_sum(at * ua);
-        const double ft = fs - au;
-        if (lane == 0) {
-            const int ev = S.evals[cell] + 1;
-            S.evals[cell] = ev;
-            atomicMax(&S.cnt[4], ev);
-            atomicAdd(&S.cnt[6], 1);
-        }
-
-        bool accept;
-        if (ph == PH_INIT) {
-            if (!finite) {
-                fail(S, cell, KITRT_ENOTREALIZABLE, lane);
-                continue;
-            }
-            accept = true;
-        } else {
-            const double fs0 = S.fsum[cell], f0 = S.f0[cell];
-            const double slack = 64.0 * 2.220446049250313e-16 * (fs0 + fabs(fs0 - f0));
-            accept = finite && ft <= f0 + np.c1 * lam * S.gd[cell] + slack;
-        }
-        if (!accept) {
-            const int h = S.halv[cell] + 1;
-            if (h > np.max_halvings) {
-                fail(S, cell, KITRT_ELINESEARCH, lane);
-            } else {
-                if (lane == 0) {
-                    S.halv[cell] = h;
-                    S.lam[cell] = 0.5 * lam;
-                }
-                push(list_out, cnt_out, cell, lane);
-            }
-            continue;
-        }
-
-        // accepted: store the new point and its moments
-        if (lane < n) S.alpha[off + lane] = at;
+        for (int c = 0; c < n2; ++c) V[c] = warp_sum(V[c]);
+        __syncwarp();
 #pragma unroll
         for (int c = 0; c < n2; ++c)
             if (lane == (c & 31)) Vs[c] = V[c];
         __syncwarp();
-        const double Ua = lane < n ? Vs[lane] : 0.0;
-        if (lane < n) S.U[off + lane] = Ua;
-        if (lane == 0) {
-            S.fsum[cell] = fs;
-            S.f0[cell] = ft;
-        }
-        // Hessian from Gaunt coefficients
-        for (int p = lane; p < npairs; p += 32) {
-            int a = 0;
-            while ((a + 1) * (a + 2) / 2 <= p) ++a;
-            const int b = p - a * (a + 1) / 2;
-            double h = 0.0;
-            for (int t = T.gstart[p]; t < T.gstart[p + 1]; ++t) h = fma(T.gcoef[t], Vs[T.gidx[t]], h);
-            H[a * n + b] = h;
-            H[b * n + a] = h;
-        }
+        newton_post<NN>(T, S, np, cell, ph, lam, at, ua, Vs, H, list_out, cnt_out, lane, false);
         __syncwarp();
-        if (!warp_cholesky<n>(H, lane)) {
-            fail(S, cell, KITRT_ECHOL, lane);
-            __syncwarp();
-            continue;
-        }
-        for (int a = lane; a < n; a += 32)
-            for (int b = 0; b <= a; ++b) S.L[(size_t)cell * npairs + tri_idx(a, b)] = H[a * n + b];
-        const double g = lane < n ? Ua - ua : 0.0;
-        const double d = warp_chol_solve<n>(H, -g, lane);
-        __syncwarp();
-        const double gn2 = warp_sum(g * g), un2 = warp_sum(ua * ua), gd = warp_sum(g * d);
-        if (lane < n) S.dir[off + lane] = d;
-        int iters = S.iters[cell];
-        if (ph == PH_NEWTON) ++iters;
-        if (lane == 0) S.iters[cell] = iters;
-        if (sqrt(gn2) <= np.tau * sqrt(un2)) {
-            if (lane == 0) S.phase[cell] = PH_DONE;
-            continue;
-        }
-        if (iters >= np.max_iter) {
-            fail(S, cell, KITRT_ENOCONVERGE, lane);
-            continue;
-        }
-        if (lane == 0) {
-            S.gd[cell] = gd;
-            S.lam[cell] = 1.0;
-            S.halv[cell] = 0;
-            S.phase[cell] = PH_NEWTON;
-        }
-        push(list_out, cnt_out, cell, lane);
     }
 }
 
@@ -305,7 +159,7 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
 template <int NN>
 __global__ void __launch_bounds__(kWarps * 32)
 finish_kernel(Tables T, NewtonState S, double *__restrict__ alpha_out, double *__restrict__ psi,
-              float *__restrict__ psi32, int polish, int C)
+              float *__restrict__ psi32, int polish, int compare_prev, int C)
 {
     constexpr int n = Dims<NN>::n;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -315,6 +169,12 @@ finish_kernel(Tables T, NewtonState S, double *__restrict__ alpha_out, double *_
         const bool ok = S.status[cell] == 0;
         double a = lane < n ? S.alpha[off + lane] : 0.0;
         if (ok && polish && lane < n) a += S.dir[off + lane];
+        // alpha_out still holds the previous step's alpha (and psi its ansatz) when compare_prev
+        // is set: a bitwise-unchanged alpha leaves psi as it is
+        if (compare_prev) {
+            const double prev = lane < n ? alpha_out[off + lane] : 0.0;
+            if (__all_sync(kFull, prev == a)) continue;
+        }
         if (lane < n) alpha_out[off + lane] = a;
         if (!psi && !psi32) continue;
         double av[n];
@@ -324,10 +184,65 @@ finish_kernel(Tables T, NewtonState S, double *__restrict__ alpha_out, double *_
             double z = 0.0;
 #pragma unroll
             for (int b = 0; b < n; ++b) z = fma(av[b], T.Mt[b * Qp + q], z);
-            const double e = exp(z);
-            if (psi) psi[(size_t)cell * Qp + q] = e;
-            if (psi32) psi32[(size_t)cell * Qp + q] = (float)e;
+            if (psi) {
+                const double e = exp(z);
+                psi[(size_t)cell * Qp + q] = e;
+                if (psi32) psi32[(size_t)cell * Qp + q] = (float)e;
+            } else {
+                // FP32 ansatz for the mixed modes: exact FP64 exponent split into z_hi + z_lo,
+                // exp(z) = expf(z_hi) (1 + z_lo) to FP32 accuracy without an FP64 exp
+                const float zh = (float)z;
+                const float zl = (float)(z - (double)zh);
+                psi32[(size_t)cell * Qp + q] = expf(zh) * (1.0f + zl);
+            }
         }
+    }
+}
+
+// Degree-2N moments V_c = sum_q w_q exp(alpha.m_q) m~_c(q) of given alphas, in FP64.
+template <int NN>
+__global__ void __launch_bounds__(kWarps * 32)
+moments_kernel(Tables T, const double *__restrict__ alpha, double *__restrict__ V, int C)
+{
+    constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int Qp = T.Qp;
+    for (int cell = blockIdx.x * kWarps + wib; cell < C; cell += gridDim.x * kWarps) {
+        double av[n], acc[n2];
+#pragma unroll
+        for (int a = 0; a < n; ++a) av[a] = alpha[(size_t)cell * n + a];
+#pragma unroll
+        for (int c = 0; c < n2; ++c) acc[c] = 0.0;
+        for (int q = lane; q < Qp; q += 32) {
+            double z = 0.0;
+#pragma unroll
+            for (int a = 0; a < n; ++a) z = fma(av[a], T.Mt[a * Qp + q], z);
+            const double e = T.w[q] * exp(z);
+#pragma unroll
+            for (int c = 0; c < n2; ++c) acc[c] = fma(e, T.Mt[c * Qp + q], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < n2; ++c) {
+            const double v = warp_sum(acc[c]);
+            if (lane == 0) V[(size_t)cell * n2 + c] = v;
+        }
+    }
+}
+
+// Full Hessian H_ab = sum_c G_abc V_c (row-major n x n per cell) from degree-2N moments.
+__global__ void gaunt_kernel(Tables T, const double *__restrict__ V, double *__restrict__ H, int C)
+{
+    const int n = T.n, n2 = T.n2, npairs = n * (n + 1) / 2;
+    const size_t total = (size_t)C * npairs;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int cell = (int)(i / npairs), p = (int)(i % npairs);
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= p) ++a;
+        const int b = p - a * (a + 1) / 2;
+        double h = 0.0;
+        for (int t = T.gstart[p]; t < T.gstart[p + 1]; ++t) h = fma(T.gcoef[t], V[(size_t)cell * n2 + T.gidx[t]], h);
+        H[(size_t)cell * n * n + a * n + b] = h;
+        H[(size_t)cell * n * n + b * n + a] = h;
     }
 }
 
@@ -381,6 +296,24 @@ int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cud
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
+int launch_moments_fp64(kitrt_mn *mn, const Tables &T, int C, const double *alpha, double *V, cudaStream_t s)
+{
+    const int grid = grid_for(mn, C, 8);
+    LaunchScope ls(mn, PK_OTHER, s, C);
+    KITRT_DISPATCH_N(mn->N, moments_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, alpha, V, C));
+    return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
+}
+
+int launch_gaunt(kitrt_mn *mn, const Tables &T, int C, const double *V, double *H, cudaStream_t s)
+{
+    const long total = (long)C * (T.n * (T.n + 1) / 2);
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > mn->nsm * 16) blocks = mn->nsm * 16;
+    LaunchScope ls(mn, PK_OTHER, s, C);
+    gaunt_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(T, V, H, C);
+    return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
+}
+
 int launch_ansatz(const Tables &T, int C, const double *alpha, double *psi, cudaStream_t s)
 {
     const int blocks = (C + kWarps - 1) / kWarps;
@@ -399,19 +332,24 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
 }
 
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
-                     const double *u, int k, NewtonParams np, cudaStream_t s)
+                     const double *u, int k, NewtonParams np, cudaStream_t s, bool filter)
 {
     const int grid = grid_for(mn, C, 4);
     LaunchScope ls(mn, PK_EVAL, s, 0);
-    KITRT_DISPATCH_N(mn->N, eval_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np));
+    if (filter) {
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np)));
+    } else {
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np)));
+    }
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
 int launch_finish(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
-                  double *alpha_out, double *psi, float *psi32, int polish, cudaStream_t s)
+                  double *alpha_out, double *psi, float *psi32, int polish, int compare_prev,
+                  cudaStream_t s)
 {
     const int grid = grid_for(mn, C, 8);
     LaunchScope ls(mn, PK_FINISH, s, C);
-    KITRT_DISPATCH_N(mn->N, finish_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, S, alpha_out, psi, psi32, polish, C));
+    KITRT_DISPATCH_N(mn->N, finish_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, S, alpha_out, psi, psi32, polish, compare_prev, C));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }

@@ -1,0 +1,455 @@
+// Mixed-precision evaluation of the dual of the entropy closure [Sec. 3.1, Eq. entropyOCP].
+//
+// The Hessian <m m^T e> of the dual needs the moments V_c = sum_q w_q e_q m~_c(q) of the ansatz
+// against the degree-2N basis (H_ab = sum_c G_abc V_c, Gaunt coefficients G). Its first n
+// moments are the gradient's <m e> and stay in FP64; the remaining n2 - n moments enter only the
+// Hessian and are a batched dense contraction
+//     V_hi[cells x (n2-n)] = E[cells x Q'] . M_hi[Q' x (n2-n)],   E = w exp(alpha.m)
+// that runs on the 5th-generation tensor cores: tcgen05.mma with TF32 (kind::tf32) or BF16
+// (kind::f16) operands and FP32 accumulation in tensor memory. Exponents, exp, the gradient, the
+// objective, the Cholesky factorisation and the line search stay in FP64 (newton_post).
+//
+// One CTA (256 threads) owns a tile of 128 listed cells (the MMA's M = 128 rows, row = cell).
+// The quadrature runs in chunks of 32 points: every thread computes E for one row and 16 points
+// in FP64, accumulates its FP64 gradient moments, and stores E rounded to TF32/BF16 into shared
+// memory in the canonical K-major core-matrix layout (8 rows x 16 bytes per core matrix, no
+// swizzle); the threads also stage the matching 32 columns of M_hi. One elected thread issues
+// the MMAs of the chunk and commits them to an mbarrier; chunks alternate between two buffers so
+// that the next chunk's FP64 work overlaps the tensor-core work of the previous one. Every wait
+// is bounded: on expiry the kernel records KITRT_ETIMEOUT, drains what it issued (bounded) and
+// frees its tensor memory.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "kitrt_internal.cuh"
+#include "newton_common.cuh"
+
+namespace {
+
+using namespace kitrt_dev;
+
+constexpr int kTileM = 128;   // cells per tile (MMA M)
+constexpr int kChunk = 32;    // quadrature points per chunk (MMA K per chunk)
+constexpr int kThreads = 256;
+constexpr int kWarpsM = kThreads / 32;
+constexpr long kWaitLimit = 1L << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ----- tcgen05 / mbarrier wrappers -----------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    if (BF16) {
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+            "}\n" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+            "}\n" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: start address, leading-dimension byte
+// offset (between core matrices adjacent in K), stride byte offset (between 8-row groups), and
+// the descriptor version bits of the 5th-generation tensor cores.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor: D FP32, A/B format (TF32 = 2 under kind::tf32, BF16 = 1 under
+// kind::f16), both K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, uint32_t ab)
+{
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int NN>
+struct MixedDims {
+    static constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2;
+    static constexpr int nhi = n2 - n;
+    static constexpr int NP = ((nhi + 15) / 16) * 16;          // MMA N
+    static constexpr int tcols = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);
+};
+
+// Byte layout of the dynamic shared memory of the mixed kernel.
+template <int NN, bool BF16>
+struct MixedSmem {
+    static constexpr int esz = BF16 ? 2 : 4;
+    static constexpr int T = 16 / esz;                           // elements per core-matrix row
+    static constexpr int LBO = 128;                              // K-adjacent core matrices
+    static constexpr int SBO = (kChunk / T) * 128;               // 8-row groups
+    static constexpr int A_bytes = kTileM * kChunk * esz;
+    static constexpr int B_bytes = MixedDims<NN>::NP * kChunk * esz;
+    static constexpr int off_A0 = 0;
+    static constexpr int off_A1 = off_A0 + A_bytes;
+    static constexpr int off_B0 = off_A1 + A_bytes;
+    static constexpr int off_B1 = off_B0 + B_bytes;
+    static constexpr int off_V = (off_B1 + B_bytes + 1023) / 1024 * 1024;
+    static constexpr int V_bytes = kTileM * Dims<NN>::n2 * 8;
+    static constexpr int off_H = off_V + V_bytes;
+    static constexpr int H_bytes = kWarpsM * Dims<NN>::n * Dims<NN>::n * 8;
+    static constexpr int off_bar = off_H + H_bytes;
+    static constexpr int total = off_bar + 64;
+    static constexpr int kmma = BF16 ? 16 : 8;                   // MMA K
+    // byte offset of element (row r, k) inside an operand chunk
+    static __device__ __forceinline__ int elem_off(int r, int k)
+    {
+        return (r >> 3) * SBO + (k / T) * LBO + (r & 7) * 16 + (k % T) * esz;
+    }
+};
+
+template <int NN, bool BF16, bool MOMENTS_ONLY>
+__global__ void __launch_bounds__(kThreads, 1)
+eval_mixed_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
+                  const void *__restrict__ Mhi, const double *__restrict__ alpha_in,
+                  double *__restrict__ Vout, int C)
+{
+    using D = MixedDims<NN>;
+    using L = MixedSmem<NN, BF16>;
+    constexpr int n = D::n, n2 = D::n2, NP = D::NP;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    double *sV = (double *)(smem + L::off_V);
+    uint64_t *bar = (uint64_t *)(smem + L::off_bar);
+    uint32_t *tmem_slot = (uint32_t *)(smem + L::off_bar + 16);
+    int *abort_flag = (int *)(smem + L::off_bar + 24);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Qp = T.Qp, nchunks = Qp / kChunk;
+
+    int cnt_in;
+    const int32_t *list_in = nullptr;
+    int32_t *list_out = nullptr, *cnt_out = nullptr;
+    if (MOMENTS_ONLY) {
+        cnt_in = C;
+    } else {
+        list_in = S.list[k & 1];
+        list_out = S.list[(k + 1) & 1];
+        cnt_in = S.cnt[k % 3];
+        cnt_out = &S.cnt[(k + 1) % 3];
+        if (blockIdx.x == 0 && tid == 0) S.cnt[(k + 2) % 3] = 0;
+    }
+    if ((int)blockIdx.x * kTileM >= cnt_in) return;  // no tile for this CTA (uniform per CTA)
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, D::tcols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = instr_desc(kTileM, NP, BF16 ? 1u : 2u);
+    uint32_t commits[2] = {0, 0}, waited[2] = {0, 0};
+    const int r = tid & (kTileM - 1), h = tid >> 7;  // row of this thread, half of each chunk
+
+    for (int tile = blockIdx.x; tile * kTileM < cnt_in; tile += gridDim.x) {
+        const int base = tile * kTileM;
+        const int rows = min(kTileM, cnt_in - base);
+        int cell = -1;
+        if (r < rows) cell = MOMENTS_ONLY ? base + r : list_in[base + r];
+        bool active = cell >= 0;
+        if (!MOMENTS_ONLY && active && S.h64[cell]) active = false;  // done by the FP64 sweep
+        double at[n], U[n];
+#pragma unroll
+        for (int a = 0; a < n; ++a) {
+            U[a] = 0.0;
+            at[a] = 0.0;
+        }
+        if (active) {
+            if (MOMENTS_ONLY) {
+#pragma unroll
+                for (int a = 0; a < n; ++a) at[a] = alpha_in[(size_t)cell * n + a];
+            } else {
+                const int ph = S.phase[cell];
+                const double lam = ph == PH_NEWTON ? S.lam[cell] : 0.0;
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    const double al = S.alpha[(size_t)cell * n + a];
+                    at[a] = ph == PH_NEWTON ? fma(lam, S.dir[(size_t)cell * n + a], al) : al;
+                }
+            }
+        }
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            unsigned char *A = smem + (b ? L::off_A1 : L::off_A0);
+            unsigned char *B = smem + (b ? L::off_B1 : L::off_B0);
+            if (commits[b] > waited[b]) {
+                // the MMAs that read this buffer must have finished before it is overwritten:
+                // one thread waits on the buffer's mbarrier, the CTA barrier orders the rest
+                if (tid == 0 && !mbar_wait_bounded(&bar[b], waited[b] & 1)) *abort_flag = 1;
+                ++waited[b];
+                __syncthreads();
+                if (*abort_flag) break;  // uniform: read after the barrier
+            }
+            tc_fence_after();
+            // FP64 part: exponent, exp, weight, gradient moments; E to the operand tile
+            const int q0 = c * kChunk + h * (kChunk / 2);
+#pragma unroll 4
+            for (int j = 0; j < kChunk / 2; ++j) {
+                const int q = q0 + j;
+                double e = 0.0;
+                if (active) {
+                    double z = 0.0;
+#pragma unroll
+                    for (int a = 0; a < n; ++a) z = fma(at[a], T.Mt[a * Qp + q], z);
+                    e = T.w[q] * exp(z);
+#pragma unroll
+                    for (int a = 0; a < n; ++a) U[a] = fma(e, T.Mt[a * Qp + q], U[a]);
+                }
+                const int kk = h * (kChunk / 2) + j;
+                if (BF16) {
+                    *(__nv_bfloat16 *)(A + L::elem_off(r, kk)) = __float2bfloat16_rn((float)e);
+                } else {
+                    uint32_t t32;
+                    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t32) : "f"((float)e));
+                    *(uint32_t *)(A + L::elem_off(r, kk)) = t32;
+                }
+            }
+            // stage the chunk of M_hi (row-major [NP x Qp] in global, 16-byte pieces)
+            constexpr int per16 = L::T;  // elements per 16 bytes
+            constexpr int pieces = NP * (kChunk / per16);
+            for (int p = tid; p < pieces; p += kThreads) {
+                const int row = p / (kChunk / per16), kp = (p % (kChunk / per16)) * per16;
+                const uint4 v = *(const uint4 *)((const unsigned char *)Mhi +
+                                                 ((size_t)row * Qp + c * kChunk + kp) * L::esz);
+                *(uint4 *)(B + L::elem_off(row, kp)) = v;
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint64_t ad = smem_desc(smem_u32(A), L::LBO, L::SBO);
+                const uint64_t bd = smem_desc(smem_u32(B), L::LBO, L::SBO);
+#pragma unroll
+                for (int j = 0; j < kChunk / L::kmma; ++j) {
+                    // each MMA covers 32 bytes of K = two core matrices = 2 * LBO bytes
+                    const uint64_t step = (uint64_t)((j * 2 * L::LBO) >> 4);
+                    mma_issue<BF16>(tmem, ad + step, bd + step, idesc, (c > 0 || j > 0) ? 1u : 0u);
+                }
+                mma_commit(&bar[b]);
+            }
+            ++commits[b];
+        }
+        // drain: every MMA of this tile has completed once both buffers' last commits have
+        if (tid == 0)
+            for (int b = 0; b < 2 && !*abort_flag; ++b)
+                while (commits[b] > waited[b]) {
+                    if (!mbar_wait_bounded(&bar[b], waited[b] & 1)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    ++waited[b];
+                }
+        if (tid != 0)
+            for (int b = 0; b < 2; ++b) waited[b] = commits[b];
+        __syncthreads();
+        tc_fence_after();
+        if (*abort_flag) break;
+        // gather the row moments: FP64 gradient part from both halves, tensor part from TMEM
+        double *Vr = sV + (size_t)r * n2;
+        if (h == 1) {
+#pragma unroll
+            for (int a = 0; a < n; ++a) Vr[a] = U[a];
+        }
+        __syncthreads();
+        if (h == 0) {
+#pragma unroll
+            for (int a = 0; a < n; ++a) Vr[a] += U[a];
+            const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+#pragma unroll
+            for (int c0 = 0; c0 < NP; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c0 + i < n2 - n) Vr[n + c0 + i] = (double)v[i];
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (MOMENTS_ONLY) {
+            for (int idx = tid; idx < rows * n2; idx += kThreads) {
+                const int rr = idx / n2, cc = idx % n2;
+                Vout[(size_t)(base + rr) * n2 + cc] = sV[(size_t)rr * n2 + cc];
+            }
+        } else {
+            double *H = (double *)(smem + L::off_H) + warp * n * n;
+            for (int rr = warp; rr < rows; rr += kWarpsM) {
+                const int cl = list_in[base + rr];
+                if (S.h64[cl]) continue;
+                const int ph = S.phase[cl];
+                const double lam = ph == PH_NEWTON ? S.lam[cl] : 0.0;
+                const size_t off = (size_t)cl * n;
+                const double ua = lane < n ? u[off + lane] : 0.0;
+                const double al = lane < n ? S.alpha[off + lane] : 0.0;
+                const double di = (ph == PH_NEWTON && lane < n) ? S.dir[off + lane] : 0.0;
+                const double atl = lane < n ? (ph == PH_NEWTON ? fma(lam, di, al) : al) : 0.0;
+                newton_post<NN>(T, S, np, cl, ph, lam, atl, ua, sV + (size_t)rr * n2, H, list_out,
+                                cnt_out, lane, true);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+    // an aborted tile may still have MMAs in flight: wait for them (bounded) before freeing TMEM
+    if (tid == 0 && *abort_flag) {
+        if (!MOMENTS_ONLY) atomicExch(&S.cnt[7], KITRT_ETIMEOUT);
+        else atomicExch((int *)Vout + 1, 0x7ff80000);  // poison the first moment (NaN high word)
+        for (int b = 0; b < 2; ++b)
+            while (commits[b] > waited[b]) {
+                if (!mbar_wait_bounded(&bar[b], waited[b] & 1)) break;
+                ++waited[b];
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, D::tcols);
+}
+
+template <int NN, bool BF16, bool MO>
+int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const double *u, int k,
+                      NewtonParams np, const double *alpha_in, double *Vout, int C, cudaStream_t s)
+{
+    using L = MixedSmem<NN, BF16>;
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(eval_mixed_kernel<NN, BF16, MO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 L::total) != cudaSuccess)
+            return KITRT_ECUDA;
+        configured = true;
+    }
+    const int tiles = (C + kTileM - 1) / kTileM;
+    const int grid = tiles < mn->nsm ? (tiles > 0 ? tiles : 1) : mn->nsm;
+    eval_mixed_kernel<NN, BF16, MO><<<grid, kThreads, L::total, s>>>(
+        T, S, u, k, np, BF16 ? (const void *)mn->d_Mhi16 : (const void *)mn->d_Mhi32, alpha_in, Vout, C);
+    return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
+}
+
+template <bool MO>
+int launch_mixed_dispatch(kitrt_mn *mn, const Tables &T, const NewtonState &S, const double *u, int k,
+                          NewtonParams np, const double *alpha_in, double *Vout, int C, bool bf16,
+                          cudaStream_t s)
+{
+#define MIXED_CASE(NNv)                                                                                  \
+    case NNv:                                                                                            \
+        return bf16 ? launch_mixed_impl<NNv, true, MO>(mn, T, S, u, k, np, alpha_in, Vout, C, s)        \
+                    : launch_mixed_impl<NNv, false, MO>(mn, T, S, u, k, np, alpha_in, Vout, C, s);
+    switch (mn->N) {
+        MIXED_CASE(1)
+        MIXED_CASE(2)
+        MIXED_CASE(3)
+        MIXED_CASE(4)
+        MIXED_CASE(5)
+    default: return KITRT_EINVAL;
+    }
+#undef MIXED_CASE
+}
+
+}  // namespace
+
+int launch_eval_mixed(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u, int k,
+                      NewtonParams np, cudaStream_t s)
+{
+    LaunchScope ls(mn, PK_EVAL_MIXED, s, 0);
+    return launch_mixed_dispatch<false>(mn, T, S, u, k, np, nullptr, nullptr, C,
+                                        mn->p.mode == KITRT_MIXED_BF16, s);
+}
+
+int launch_moments_mixed(kitrt_mn *mn, const Tables &T, int C, const double *alpha, double *Vout,
+                         cudaStream_t s)
+{
+    LaunchScope ls(mn, PK_OTHER, s, C);
+    NewtonState S{};
+    NewtonParams np{};
+    return launch_mixed_dispatch<true>(mn, T, S, nullptr, 0, np, alpha, Vout, C,
+                                       mn->p.mode == KITRT_MIXED_BF16, s);
+}

@@ -150,7 +150,7 @@ extern "C" int32_t kitrt_closure_noalloc(const kitrt_mn *mn, const double *u, do
         if (cnt[k % 3] == 0) break;
         if (k >= max_launch) return KITRT_ETIMEOUT;
     }
-    rc = launch_finish(&view, T, S, C, alpha, nullptr, nullptr, mn->p.polish, s);
+    rc = launch_finish(&view, T, S, C, alpha, nullptr, nullptr, mn->p.polish, 0, s);
     if (rc) return rc;
     if (status && cudaMemcpyAsync(status, S.status, sizeof(int32_t) * C, cudaMemcpyDeviceToDevice,
                                   s) != cudaSuccess)

@@ -76,6 +76,73 @@ flux_update_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restr
     }
 }
 
+// FP32 variant for the mixed modes: FP32 ansatz, FP32 upwind sums, Kahan-compensated FP32
+// projection per lane, FP64 warp reduction and update.
+template <int NN>
+__global__ void __launch_bounds__(kWarps * 32)
+flux_update32_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restrict__ nrm,
+                     const double *__restrict__ area, const float *__restrict__ psi,
+                     double *__restrict__ u, const double *__restrict__ sa,
+                     const double *__restrict__ ss, const double *__restrict__ qs, double dt,
+                     int bc, int C)
+{
+    constexpr int n = (NN + 1) * (NN + 2) / 2;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int Qp = T.Qp;
+    for (int i = blockIdx.x * kWarps + wib; i < C; i += gridDim.x * kWarps) {
+        const int4 nb = nbr[i];
+        const float nx0 = (float)nrm[6 * (size_t)i], ny0 = (float)nrm[6 * (size_t)i + 1];
+        const float nx1 = (float)nrm[6 * (size_t)i + 2], ny1 = (float)nrm[6 * (size_t)i + 3];
+        const float nx2 = (float)nrm[6 * (size_t)i + 4], ny2 = (float)nrm[6 * (size_t)i + 5];
+        const float *pi_row = psi + (size_t)i * Qp;
+        float F[n], Fc[n];
+#pragma unroll
+        for (int a = 0; a < n; ++a) F[a] = Fc[a] = 0.0f;
+        for (int q = lane; q < Qp; q += 32) {
+            const float pi = pi_row[q];
+            const float wx = T.wox32[q], wy = T.woy32[q];
+            const float ghost = bc == 0 ? pi : 0.0f;
+            float s = 0.0f;
+            {
+                const float d = fmaf(wx, nx0, wy * ny0);
+                const float up = d > 0.0f ? pi : (nb.x >= 0 ? psi[(size_t)nb.x * Qp + q] : ghost);
+                s = fmaf(d, up, s);
+            }
+            {
+                const float d = fmaf(wx, nx1, wy * ny1);
+                const float up = d > 0.0f ? pi : (nb.y >= 0 ? psi[(size_t)nb.y * Qp + q] : ghost);
+                s = fmaf(d, up, s);
+            }
+            {
+                const float d = fmaf(wx, nx2, wy * ny2);
+                const float up = d > 0.0f ? pi : (nb.z >= 0 ? psi[(size_t)nb.z * Qp + q] : ghost);
+                s = fmaf(d, up, s);
+            }
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                const float y = fmaf(T.Mt32[a * Qp + q], s, -Fc[a]);
+                const float t = F[a] + y;
+                Fc[a] = (t - F[a]) - y;
+                F[a] = t;
+            }
+        }
+        double Fa = 0.0;
+#pragma unroll
+        for (int a = 0; a < n; ++a) {
+            double v = (double)F[a] - (double)Fc[a];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            if (lane == a) Fa = v;
+        }
+        const double u0 = u[(size_t)i * n];
+        if (lane < n) {
+            const double ua = u[(size_t)i * n + lane];
+            const double R = -sa[i] * ua - ss[i] * (ua - (lane == 0 ? u0 : 0.0)) + qs[i] * T.mbar[lane];
+            u[(size_t)i * n + lane] = ua - dt / area[i] * Fa + dt * R;
+        }
+    }
+}
+
 }  // namespace
 
 int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
@@ -93,7 +160,7 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
             flux_update_kernel<NN, double><<<grid, kWarps * 32, 0, s>>>(                        \
                 T, m->d_nbr, m->d_nrm, m->d_area, psi, u, sa, ss, q, dt, bc, C);               \
         else                                                                                   \
-            flux_update_kernel<NN, float><<<grid, kWarps * 32, 0, s>>>(                         \
+            flux_update32_kernel<NN><<<grid, kWarps * 32, 0, s>>>(                              \
                 T, m->d_nbr, m->d_nrm, m->d_area, psi32, u, sa, ss, q, dt, bc, C);             \
         break;
     switch (mn->N) {

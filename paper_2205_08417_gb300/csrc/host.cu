@@ -188,6 +188,8 @@ Tables kitrt_mn::tables() const
     T.gcoef = d_gcoef;
     T.Mt32 = d_Mt32;
     T.w32 = d_w32;
+    T.wox32 = d_wox32;
+    T.woy32 = d_woy32;
     return T;
 }
 
@@ -435,6 +437,25 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     gstart[mn->npairs] = (int32_t)gidx.size();
     mn->gaunt_nnz = (int)gidx.size();
     std::vector<float> Mt32(Mt.begin(), Mt.end()), w32(w.begin(), w.end());
+    std::vector<float> wox32(wox.begin(), wox.end()), woy32(woy.begin(), woy.end());
+    // tensor-core operand of the mixed modes: the degree N+1..2N basis functions (rows n..n2-1
+    // of Mt), padded to a multiple of 16 rows, rounded to TF32 (nearest, ties away) and to BF16
+    // (nearest even)
+    const int nhi = n2 - n, NP = (nhi + 15) / 16 * 16;
+    std::vector<float> Mhi32((size_t)NP * Qp, 0.0f);
+    std::vector<unsigned short> Mhi16((size_t)NP * Qp, 0);
+    for (int c = 0; c < nhi; ++c)
+        for (int q = 0; q < Qp; ++q) {
+            float f = (float)Mt[(size_t)(n + c) * Qp + q];
+            uint32_t bits;
+            memcpy(&bits, &f, 4);
+            uint32_t t = (bits + 0x1000u) & ~0x1FFFu;
+            float ft;
+            memcpy(&ft, &t, 4);
+            Mhi32[(size_t)c * Qp + q] = ft;
+            uint32_t rb = bits + 0x7FFFu + ((bits >> 16) & 1u);
+            Mhi16[(size_t)c * Qp + q] = (unsigned short)(rb >> 16);
+        }
     TRY(dev_upload(mn, &mn->d_Mt, Mt));
     TRY(dev_upload(mn, &mn->d_w, w));
     TRY(dev_upload(mn, &mn->d_wox, wox));
@@ -445,6 +466,10 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_upload(mn, &mn->d_gcoef, gcoef));
     TRY(dev_upload(mn, &mn->d_Mt32, Mt32));
     TRY(dev_upload(mn, &mn->d_w32, w32));
+    TRY(dev_upload(mn, &mn->d_wox32, wox32));
+    TRY(dev_upload(mn, &mn->d_woy32, woy32));
+    TRY(dev_upload(mn, &mn->d_Mhi32, Mhi32));
+    TRY(dev_upload(mn, &mn->d_Mhi16, Mhi16));
 
     // workspace
     const size_t C = mesh->C;
@@ -466,6 +491,11 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_alloc(mn, &S.list[1], C));
     TRY(dev_alloc(mn, &S.cnt, 8));
     TRY(dev_alloc(mn, &mn->d_psi, C * Qp));
+    if (p.mode != KITRT_FP64) {
+        TRY(dev_alloc(mn, &mn->d_psi32, C * Qp));
+        TRY(dev_alloc(mn, &S.h64, C));
+        TRY(dev_alloc(mn, &S.gnorm, C));
+    }
     if (cudaMallocHost(&mn->h_cnt, 8 * sizeof(int32_t)) != cudaSuccess) {
         kitrt_mn_destroy(mn);
         return KITRT_ENOMEM;
@@ -523,6 +553,10 @@ int32_t kitrt_isotropic_alpha(kitrt_mn *mn, const double *u, double *alpha, void
 // Newton driver (shared by kitrt_closure and kitrt_step)
 // ------------------------------------------------------------------------------------------
 
+// The polish step (one more full Newton step once the test passes) needs the exact Hessian: it
+// is applied in FP64 mode only.
+static int polish_of(const kitrt_mn *mn) { return mn->p.polish && mn->p.mode == KITRT_FP64; }
+
 // Runs the closure of every cell to completion. first = 1 starts from alpha_in (evaluation
 // first); first = 0 reuses the state of the previous closure as the predictor. Leaves the
 // converged state in mn->st; returns the first failure status or KITRT_OK.
@@ -531,7 +565,7 @@ static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, in
 {
     const int C = mn->mesh->C;
     const Tables T = mn->tables();
-    NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, mn->p.polish};
+    NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, polish_of(mn)};
     CUDA_OK(cudaMemsetAsync(mn->st.cnt, 0, 8 * sizeof(int32_t), s));
     int rc = launch_begin(mn, T, mn->st, C, u, alpha_in, first, np, s);
     if (rc) return rc;
@@ -540,16 +574,25 @@ static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, in
     int k = 0;
     for (;;) {
         for (int b = 0; b < batch; ++b, ++k) {
-            rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s);
+            if (mn->p.mode == KITRT_FP64) {
+                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s);
+            } else {
+                // FP64 sweep of the cells handed over in earlier rounds, then the tensor-core sweep
+                // of the others (cells it hands over now wait for the next round, so no cell is
+                // evaluated twice in one round)
+                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, true);
+                if (!rc) rc = launch_eval_mixed(mn, T, mn->st, C, u, k, np, s);
+            }
             if (rc) return rc;
         }
         CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CUDA_OK(cudaStreamSynchronize(s));
+        if (mn->h_cnt[7]) return mn->h_cnt[7];
         int active = mn->h_cnt[k % 3];
         if (active == 0) break;
         if (k >= max_launch) return KITRT_ETIMEOUT;
     }
-    if (mn->prof_on) mn->prof_units[PK_EVAL] += mn->h_cnt[6];
+    if (mn->prof_on) mn->prof_units[mn->p.mode == KITRT_FP64 ? PK_EVAL : PK_EVAL_MIXED] += mn->h_cnt[6];
     if (stats) {
         stats->closures += C;
         stats->evaluations += mn->h_cnt[6];
@@ -577,7 +620,7 @@ int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *sta
     const int64_t launches0 = mn->launch_count;
     int rc = run_closure(mn, u, alpha, 1, s, stats);
     int rc2 = launch_finish(mn, mn->tables(), mn->st, mn->mesh->C, alpha, nullptr, nullptr,
-                            mn->p.polish, s);
+                            polish_of(mn), 0, s);
     if (status)
         CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * mn->mesh->C,
                                 cudaMemcpyDeviceToDevice, s));
@@ -612,9 +655,12 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
     for (int32_t it = 0; it < nsteps; ++it) {
         rc = run_closure(mn, u, alpha, it == 0, s, stats);
         if (rc) break;
-        rc = launch_finish(mn, T, mn->st, C, alpha, mn->d_psi, nullptr, mn->p.polish, s);
+        const bool fp64 = mn->p.mode == KITRT_FP64;
+        rc = launch_finish(mn, T, mn->st, C, alpha, fp64 ? mn->d_psi : nullptr,
+                           fp64 ? nullptr : mn->d_psi32, polish_of(mn), it > 0, s);
         if (rc) break;
-        rc = launch_flux_update(mn, T, C, mn->d_psi, nullptr, u, sigma_a, sigma_s, q, dt, mn->p.bc, s);
+        rc = launch_flux_update(mn, T, C, fp64 ? mn->d_psi : nullptr, fp64 ? nullptr : mn->d_psi32,
+                                u, sigma_a, sigma_s, q, dt, mn->p.bc, s);
         if (rc) break;
     }
     if (status)
@@ -625,6 +671,22 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
         CUDA_OK(cudaStreamSynchronize(s));
     }
     return rc;
+}
+
+int32_t kitrt_hessian(kitrt_mn *mn, const double *alpha, double *H, void *stream)
+{
+    if (!mn || !alpha || !H) return KITRT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int C = mn->mesh->C;
+    const Tables T = mn->tables();
+    if (!mn->d_V && cudaMalloc(&mn->d_V, sizeof(double) * (size_t)C * mn->n2) != cudaSuccess)
+        return KITRT_ENOMEM;
+    if (mn->d_V && std::find(mn->allocs.begin(), mn->allocs.end(), (void *)mn->d_V) == mn->allocs.end())
+        mn->allocs.push_back(mn->d_V);
+    int rc = mn->p.mode == KITRT_FP64 ? launch_moments_fp64(mn, T, C, alpha, mn->d_V, s)
+                                      : launch_moments_mixed(mn, T, C, alpha, mn->d_V, s);
+    if (rc) return rc;
+    return launch_gaunt(mn, T, C, mn->d_V, H, s);
 }
 
 int32_t kitrt_profile_enable(kitrt_mn *mn, int32_t on)

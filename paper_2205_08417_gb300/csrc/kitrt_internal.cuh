@@ -39,6 +39,7 @@ struct Tables {
     const double *gcoef;      // [nnz] <m_a m_b m~_c>
     const float *Mt32;        // [n2 x Qp] FP32 copy
     const float *w32;
+    const float *wox32, *woy32;  // FP32 copies of w * Omega
 };
 
 struct NewtonState {
@@ -55,6 +56,8 @@ struct NewtonState {
     int32_t *halv;     // [C] halvings in the current iteration
     int32_t *evals;    // [C] evaluations in this closure
     int32_t *status;   // [C]
+    int32_t *h64;      // [C] mixed modes: 1 = this cell evaluates its Hessian in FP64 (else NULL)
+    double *gnorm;     // [C] mixed modes: ||g|| at the last accepted point (else NULL)
     int32_t *list[2];  // active cell lists (ping-pong)
     int32_t *cnt;      // [8]: cnt[0..2] rotating list counters, cnt[3] failures, cnt[4] max evals,
                        //       cnt[5] fallbacks
@@ -86,6 +89,10 @@ struct kitrt_mn {
     double *d_mbar = nullptr, *d_gcoef = nullptr;
     int32_t *d_gstart = nullptr, *d_gidx = nullptr;
     float *d_Mt32 = nullptr, *d_w32 = nullptr;
+    float *d_Mhi32 = nullptr;            // [NP x Qp] TF32-rounded degree-(N+1..2N) basis (mixed)
+    unsigned short *d_Mhi16 = nullptr;   // [NP x Qp] BF16 copy
+    float *d_wox32 = nullptr, *d_woy32 = nullptr;
+    double *d_V = nullptr;               // [C x n2] moments scratch (kitrt_hessian)
     // workspace
     NewtonState st{};
     double *d_psi = nullptr;   // [C x Qp] FP64 ansatz
@@ -117,10 +124,19 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                  const double *u, const double *alpha_in, int first, NewtonParams np,
                  cudaStream_t s);
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
-                     const double *u, int k, NewtonParams np, cudaStream_t s);
+                     const double *u, int k, NewtonParams np, cudaStream_t s,
+                     bool filter = false);
 int launch_finish(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
-                  double *alpha_out, double *psi, float *psi32, int polish, cudaStream_t s);
+                  double *alpha_out, double *psi, float *psi32, int polish, int compare_prev,
+                  cudaStream_t s);
 int launch_ansatz(const Tables &T, int C, const double *alpha, double *psi, cudaStream_t s);
+int launch_moments_fp64(kitrt_mn *mn, const Tables &T, int C, const double *alpha, double *V,
+                        cudaStream_t s);
+int launch_gaunt(kitrt_mn *mn, const Tables &T, int C, const double *V, double *H, cudaStream_t s);
+int launch_eval_mixed(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u,
+                      int k, NewtonParams np, cudaStream_t s);
+int launch_moments_mixed(kitrt_mn *mn, const Tables &T, int C, const double *alpha, double *Vout,
+                         cudaStream_t s);
 int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
                        const float *psi32, double *u, const double *sa, const double *ss,
                        const double *q, double dt, int bc, cudaStream_t s);

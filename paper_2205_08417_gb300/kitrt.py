@@ -73,6 +73,7 @@ SIGNATURES = {
     "kitrt_mn_quadrature": (C.c_int32, [_vp, _dp, _dp, _dp]),
     "kitrt_isotropic_alpha": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_closure": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Stats)]),
+    "kitrt_hessian": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_ansatz": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_step": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int32, _vp, _vp,
                                C.POINTER(Stats)]),
@@ -231,6 +232,14 @@ class MNSolver:
         if check:
             _check(rc, "kitrt_closure_noalloc")
         return rc
+
+    def hessian(self, alpha):
+        import torch
+        n = self.n
+        H = torch.empty((alpha.shape[0], n, n), dtype=torch.float64, device=alpha.device)
+        _check(_lib().kitrt_hessian(self.handle, _dev(alpha, torch.float64), _dev(H), _stream()),
+               "kitrt_hessian")
+        return H
 
     def ansatz(self, alpha):
         import torch

@@ -1,0 +1,176 @@
+"""GPU parity of the mixed-precision paths (tensor-core Hessian moments in TF32 or BF16, FP64
+gradient / Cholesky / line search, FP32 ansatz and flux) against the CPU oracle, through the C ABI.
+
+Bars: the Hessian within the input rounding of its tensor-core operands (TF32 2^-11, BF16 2^-8
+relative per operand, accumulated in FP32); the closure to the same tolerance as FP64 (its
+gradient and test are FP64); the step within 1e-5 relative L2 on the zeroth moment."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2205_08417_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MIXED = ["mixed_tf32", "mixed_bf16"]
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_08417_gb300 import build, kitrt
+    build.build()
+    return kitrt
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def vmf_u(T, count, seed, kappa_hi=20.0):
+    mu, phi, w, ox, oy = O.quadrature(T.order)
+    dirs = np.stack([ox, oy, mu], axis=1)
+    c, k, wt = synth.vmf_mixtures(count, seed, kappa_hi=kappa_hi)
+    psi = synth.vmf_density(dirs, c, k, wt)
+    scale = np.exp(np.random.default_rng(seed).uniform(-3, 2, size=count))
+    return (psi * scale[:, None]) @ (T.w[:, None] * T.M)
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-13), ("mixed_tf32", 3e-3), ("mixed_bf16", 2.5e-2)])
+@pytest.mark.parametrize("N,order", [(1, 4), (2, 10), (3, 20), (5, 30)])
+def test_hessian_matches_definition(K, mode, tol, N, order):
+    """H = <m m^T exp(alpha.m)> on the oracle's full rule vs the library (FP64, or tensor-core
+    moments); ragged cell count (not a multiple of the 128-row tile)."""
+    m = synth.jittered_mesh(18, 0.0, 1.0, seed=3)
+    mesh = K.Mesh(m.xy, m.tri)
+    C = mesh.ncells
+    assert C % 128 != 0
+    s = K.MNSolver(mesh, N, order, mode=mode)
+    T = O.Tables(N, order)
+    u = vmf_u(T, C, seed=30 + N)
+    a = O.isotropic_alpha(T, u)
+    O.closure(T, u, a)
+    Hg = s.hessian(dev(a)).cpu().numpy()
+    worst = 0.0
+    for i in range(C):
+        e = T.w * np.exp(T.M @ a[i])
+        H = T.M.T @ (e[:, None] * T.M)
+        worst = max(worst, np.abs(Hg[i] - H).max() / np.abs(H).max())
+    assert worst <= tol, worst
+
+
+@pytest.mark.parametrize("mode", MIXED)
+@pytest.mark.parametrize("N,order", [(2, 10), (3, 20), (5, 30)])
+def test_mixed_closure_matches_oracle(K, mode, N, order):
+    T = O.Tables(N, order)
+    m = synth.jittered_mesh(20, 0.0, 1.0, seed=4)
+    mesh = K.Mesh(m.xy, m.tri)
+    C = mesh.ncells
+    s = K.MNSolver(mesh, N, order, mode=mode)
+    u = vmf_u(T, C, seed=40 + N, kappa_hi=50.0)
+    a_or = O.isotropic_alpha(T, u)
+    st_or, _ = O.closure(T, u, a_or)
+    ud = dev(u)
+    ad = s.isotropic_alpha(ud)
+    st = torch.zeros(C, dtype=torch.int32, device="cuda")
+    rc, stats = s.closure(ud, ad, st, stats=True, check=False)
+    st = st.cpu().numpy()
+    ok = (st == 0) & (st_or == 0)
+    assert ((st == 0) == (st_or == 0)).mean() > 0.98
+    assert ok.mean() > 0.9
+    a_gpu = ad.cpu().numpy()
+    rec = np.exp(a_gpu[ok] @ T.M.T) @ (T.w[:, None] * T.M)
+    rel = np.linalg.norm(rec - u[ok], axis=1) / np.linalg.norm(u[ok], axis=1)
+    assert rel.max() <= 1e-10
+    for i in np.flatnonzero(ok):
+        e = T.w * np.exp(T.M @ a_or[i])
+        lmin = np.linalg.eigvalsh(T.M.T @ (e[:, None] * T.M))[0]
+        bound = 1e-9 * np.linalg.norm(u[i]) / lmin + 1e-12 * np.linalg.norm(a_or[i])
+        assert np.linalg.norm(a_gpu[i] - a_or[i]) <= bound
+
+
+@pytest.mark.parametrize("mode", MIXED)
+def test_mixed_line_source_m2_matches_oracle(K, mode):
+    """M_2 line source (3872 triangles, order 10), 50 steps: mixed vs the FP64 oracle on u_0."""
+    m = synth.jittered_mesh(45, -1.5, 1.5, seed=1)
+    mesh = K.Mesh(m.xy, m.tri)
+    G = O.Geometry(m.xy, m.tri)
+    T = O.Tables(2, 10)
+    u0 = synth.isotropic_moments(synth.line_source_density(G.cen), T.n)
+    C = G.C
+    dt = G.cfl_dt(0.4)
+    sa, ss, q = np.zeros(C), np.ones(C), np.zeros(C)
+    u_or = u0.copy()
+    a_or = O.isotropic_alpha(T, u_or)
+    assert O.mn_run(T, G, u_or, a_or, sa, ss, q, dt, 50)[0] == 0
+    s = K.MNSolver(mesh, 2, 10, mode=mode)
+    ud = dev(u0)
+    ad = s.isotropic_alpha(ud)
+    s.step(ud, ad, dev(sa), dev(ss), dev(q), dt=dt, nsteps=50)
+    u_gpu = ud.cpu().numpy()
+    err0 = rel_l2(u_gpu[:, 0], u_or[:, 0])
+    print(mode, "u0 rel L2", err0, "u rel L2", rel_l2(u_gpu, u_or))
+    assert err0 <= 1e-5
+
+
+@pytest.mark.parametrize("mode", MIXED)
+def test_mixed_blocks_vacuum_m3_matches_oracle(K, mode):
+    N, order = 3, 10
+    m = synth.jittered_mesh(30, 0.0, 7.0, seed=3)
+    mesh = K.Mesh(m.xy, m.tri)
+    G = O.Geometry(m.xy, m.tri)
+    T = O.Tables(N, order)
+    blk, sab, ssb = synth.block_coefficients(G.cen, 0.0, 7.0, 7, seed=3)
+    sa, ss = sab[blk], ssb[blk]
+    q = np.where(blk == 24, 1.0, 0.0)
+    u0 = np.zeros((G.C, T.n))
+    u0[:, 0] = 1e-4 / math.sqrt(4 * math.pi)
+    dt = G.cfl_dt(0.4)
+    u_or = u0.copy()
+    a_or = O.isotropic_alpha(T, u_or)
+    assert O.mn_run(T, G, u_or, a_or, sa, ss, q, dt, 10, bc=1)[0] == 0
+    s = K.MNSolver(mesh, N, order, mode=mode, bc="vacuum")
+    ud = dev(u0)
+    ad = s.isotropic_alpha(ud)
+    s.step(ud, ad, dev(sa), dev(ss), dev(q), dt=dt, nsteps=10)
+    assert rel_l2(ud.cpu().numpy()[:, 0], u_or[:, 0]) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", MIXED)
+def test_mixed_d2_size_sampled_against_oracle(K, mode):
+    """Full-size M_3 line source (~100k triangles, order 20) in the benchmark's launch
+    configuration: 3 mixed steps, then one more checked on sampled cells against the oracle (each
+    sampled cell recomputed on a submesh of it and its neighbours)."""
+    m = synth.jittered_mesh(224, -1.5, 1.5, seed=2)
+    mesh = K.Mesh(m.xy, m.tri)
+    G = O.Geometry(m.xy, m.tri)
+    T = O.Tables(3, 20)
+    u0 = synth.isotropic_moments(synth.line_source_density(G.cen), T.n)
+    C = G.C
+    dt = G.cfl_dt(0.4)
+    sa, ss, q = np.zeros(C), np.ones(C), np.zeros(C)
+    s = K.MNSolver(mesh, 3, 20, mode=mode)
+    ud = dev(u0)
+    ad = s.isotropic_alpha(ud)
+    s.step(ud, ad, dev(sa), dev(ss), dev(q), dt=dt, nsteps=3)
+    u_start, a_start = ud.cpu().numpy().copy(), ad.cpu().numpy().copy()
+    s.step(ud, ad, dev(sa), dev(ss), dev(q), dt=dt, nsteps=1)
+    u_gpu = ud.cpu().numpy()
+    rng = np.random.default_rng(1)
+    front = np.flatnonzero((G.cen ** 2).sum(axis=1) < 0.05)
+    sample = np.unique(np.concatenate([rng.choice(C, 150, replace=False),
+                                       rng.choice(front, min(150, front.size), replace=False)]))
+    cells = np.unique(np.concatenate([sample, G.nbr[sample][G.nbr[sample] >= 0]]))
+    Gs = O.Geometry(m.xy, m.tri[cells])
+    us, als = u_start[cells].copy(), a_start[cells].copy()
+    O.mn_run(T, Gs, us, als, sa[cells], ss[cells], q[cells], dt, 1)
+    pos = np.searchsorted(cells, sample)
+    assert rel_l2(u_gpu[sample, 0], us[pos, 0]) <= 1e-5
