@@ -41,14 +41,17 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", default="fp64", help="headline closure mode")
-    ap.add_argument("--compare", default="", help="comma list of extra modes to time")
+    ap.add_argument("--mode", default="mixed_tf32", help="headline closure mode")
+    ap.add_argument("--compare", default="fp64,mixed_bf16", help="comma list of extra modes to time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synth.WORKLOADS key (the default is the benchmarked configuration)")
     ap.add_argument("--t-start", type=float, default=0.25,
                     help="simulated time reached by untimed set-up steps before warm-up")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tau", type=float, default=1e-10, help="Newton tolerance of the FP64 mode")
+    ap.add_argument("--tau-mixed", type=float, default=1e-8,
+                    help="Newton tolerance of the mixed modes (matched to their FP32 ansatz)")
     return ap.parse_args()
 
 
@@ -172,9 +175,9 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-def run_mode(K, torch, W, mode, steps, warmup, t_start, e2e=True):
+def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True):
     mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
-    s = K.MNSolver(mesh, W["N"], W["order"], mode=mode)
+    s = K.MNSolver(mesh, W["N"], W["order"], mode=mode, tau=tau)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     u = d(W["u0"])
     alpha = s.isotropic_alpha(u)
@@ -182,9 +185,10 @@ def run_mode(K, torch, W, mode, steps, warmup, t_start, e2e=True):
     geo = mesh.geometry()
     dt = 0.4 * geo["min_inradius"]
     setup = int(round(t_start / dt))
+    before = 0
     if setup:
-        s.step(u, alpha, sa, ss, q, dt=dt, nsteps=setup)
-    s.step(u, alpha, sa, ss, q, dt=dt, nsteps=warmup)
+        before += s.step(u, alpha, sa, ss, q, dt=dt, nsteps=setup, stats=True)[1]["launches"]
+    before += s.step(u, alpha, sa, ss, q, dt=dt, nsteps=warmup, stats=True)[1]["launches"]
     torch.cuda.synchronize()
     s.profile(True)
     stream = torch.cuda.current_stream()
@@ -197,7 +201,8 @@ def run_mode(K, torch, W, mode, steps, warmup, t_start, e2e=True):
     ms = e0.elapsed_time(e1)
     prof = s.profile_read()
     s.profile(False)
-    out = dict(mode=mode, ms=ms, stats=st, prof=prof, dt=dt, setup=setup, u=u.cpu().numpy(),
+    out = dict(mode=mode, ms=ms, stats=st, prof=prof, dt=dt, setup=setup, launches_before=before,
+               u=u.cpu().numpy(),
                alpha=alpha.cpu().numpy(), nbr=geo["nbr"], solver=s, mesh=mesh)
     if e2e:
         C, n = W["C"], W["n"]
@@ -265,7 +270,9 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
         cs = ClockSampler(local) if mode == args.mode else None
-        r = run_mode(K, torch, W, mode, args.steps, args.warmup, args.t_start, e2e=not args.no_e2e)
+        tau = args.tau if mode == "fp64" else args.tau_mixed
+        r = run_mode(K, torch, W, mode, args.steps, args.warmup, args.t_start, tau, e2e=not args.no_e2e)
+        r["tau"] = tau
         if cs is not None:
             clocks = cs.stop()
         results[mode] = r
@@ -284,7 +291,8 @@ def main():
     n, Qf = W["n"], W["order"] ** 2  # folded points Q' = Q/2 = order^2
     work = head["solver"].work()
     fl = work["flops_per_eval"]
-    pe = head["prof"].get("closure_eval_fp64") or head["prof"].get("closure_eval_mixed")
+    ekey = "closure_eval_fp64" if args.mode == "fp64" else "closure_eval_mixed"
+    pe = head["prof"][ekey]
     achieved = pe["units"] * fl / (pe["total_ms"] / 1e3) / 1e12
     closure_ms = sum(head["prof"][k]["total_ms"] for k in head["prof"] if k.startswith("closure"))
     closures_per_s = C * args.steps / (closure_ms / 1e3)
@@ -313,13 +321,13 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "mesh_cells": C, "nmom": n,
                    "quad_points": 2 * W["order"] ** 2, "quad_points_folded": Qf,
-                   "mode": args.mode, "dt": head["dt"], "tau": 1e-10, "parallelism": f"replicas{world}",
+                   "mode": args.mode, "dt": head["dt"], "tau": head["tau"], "parallelism": f"replicas{world}",
                    "t_start": args.t_start, "setup_steps": head["setup"],
                    "l2": "working set > L2: FP64 psi (C x Q' x 8 B = "
                          f"{C * (Qf + 31) // 32 * 32 * 8 / 1e6:.0f} MB) written and re-read every step"},
         "closures_per_s": closures_per_s,
         "evaluations_per_cell_step": head["stats"]["evaluations"] / (C * args.steps),
-        "roofline": {"kernel": "closure_eval_fp64" if "closure_eval_fp64" in head["prof"] else "closure_eval_mixed",
+        "roofline": {"kernel": ekey,
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": "measured cuBLAS DGEMM 4096^3 in this run (FP64 pipe)",
@@ -329,7 +337,7 @@ def main():
         "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
                         "share": v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in head["prof"].values()))}
                     for k, v in head["prof"].items()},
-        "modes": {m: {"cell_updates_per_s": C * args.steps / (r["ms"] / 1e3),
+        "modes": {m: {"cell_updates_per_s": C * args.steps / (r["ms"] / 1e3), "tau": r["tau"],
                       "ms_per_step": r["ms"] / args.steps,
                       "evaluations_per_cell_step": r["stats"]["evaluations"] / (C * args.steps)}
                   for m, r in results.items()},
@@ -338,6 +346,7 @@ def main():
             "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["e2e_bytes"],
             "d2h_bytes_per_step": head["e2e_bytes"]},
         "gpu_launches": int(head["stats"]["launches"]),
+        "launches_before_timed": int(head["launches_before"]),
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "kitrt_internal.cuh"
+#include "kexp.cuh"
 #include "newton_common.cuh"
 
 namespace {
@@ -24,56 +25,94 @@ constexpr int kWarps = 8;  // warps per block
 // ---------------------------------------------------------------------------------------------
 // begin: start a closure. first != 0: every cell starts from alpha_in with an evaluation.
 // first == 0: the previous closure left alpha_k, its moments U, <exp>, and the Cholesky factor
-// of H(alpha_k); with the new u the gradient is U - u, so the first Newton direction needs no
-// new quadrature pass (a cell already within tolerance is done at once).
+// of H(alpha_k); with the new u the gradient is U - u. One thread per cell tests it: a cell
+// already converged (and with no polish step to take) is done at once; the others go to the
+// predictor list, where predict_kernel takes the first Newton direction from the stored factor
+// without a new quadrature pass.
 // ---------------------------------------------------------------------------------------------
+
+// Warp-aggregated append of `cell` to a list when pred holds (all active lanes call it).
+__device__ __forceinline__ void push_if(int32_t *list, int32_t *cnt, int cell, bool pred)
+{
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(act, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = cell;
+}
+
+template <int NN>
+__global__ void __launch_bounds__(256)
+begin_test_kernel(NewtonState S, const double *__restrict__ u, const double *__restrict__ alpha_in,
+                  int first, NewtonParams np, int C)
+{
+    constexpr int n = Dims<NN>::n;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < C; cell += gridDim.x * blockDim.x) {
+        const size_t off = (size_t)cell * n;
+        S.iters[cell] = 0;
+        S.halv[cell] = 0;
+        S.evals[cell] = 0;
+        S.status[cell] = 0;
+        if (S.h64) S.h64[cell] = 0;
+        if (S.gnorm) S.gnorm[cell] = INFINITY;
+        bool to_eval = false, to_predict = false;
+        if (first) {
+#pragma unroll
+            for (int a = 0; a < n; ++a) S.alpha[off + a] = alpha_in[off + a];
+            S.phase[cell] = PH_INIT;
+            to_eval = true;
+        } else {
+            double gn2 = 0.0, un2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                const double ua = u[off + a];
+                const double g = S.U[off + a] - ua;
+                gn2 = fma(g, g, gn2);
+                un2 = fma(ua, ua, un2);
+            }
+            if (gn2 <= kRoundoff2 * un2 || (!np.polish && gn2 <= np.tau * np.tau * un2)) {
+                // already converged and no polish step to take (the polish is off, or the residual
+                // is at round-off, where it would move alpha by less than its own rounding)
+#pragma unroll
+                for (int a = 0; a < n; ++a) S.dir[off + a] = 0.0;
+                S.phase[cell] = PH_DONE;
+            } else {
+                to_predict = true;
+            }
+        }
+        push_if(S.list[0], &S.cnt[0], cell, to_eval);
+        push_if(S.list[1], &S.cnt[8], cell, to_predict);
+    }
+}
+
 template <int NN>
 __global__ void __launch_bounds__(kWarps * 32)
-begin_kernel(Tables T, NewtonState S, const double *__restrict__ u, const double *__restrict__ alpha_in,
-             int first, NewtonParams np, int C)
+predict_kernel(NewtonState S, const double *__restrict__ u, NewtonParams np)
 {
     constexpr int n = Dims<NN>::n, npairs = Dims<NN>::npairs;
     __shared__ double sH[kWarps][n * n];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     double *H = sH[wib];
-    for (int cell = blockIdx.x * kWarps + wib; cell < C; cell += gridDim.x * kWarps) {
+    const int cnt = S.cnt[8];
+    for (int it = blockIdx.x * kWarps + wib; it < cnt; it += gridDim.x * kWarps) {
+        const int cell = S.list[1][it];
         const size_t off = (size_t)cell * n;
-        if (lane == 0) {
-            S.iters[cell] = 0;
-            S.halv[cell] = 0;
-            S.evals[cell] = 0;
-            S.status[cell] = 0;
-            if (S.h64) S.h64[cell] = 0;
-            if (S.gnorm) S.gnorm[cell] = INFINITY;
-        }
-        if (first) {
-            if (lane < n) S.alpha[off + lane] = alpha_in[off + lane];
-            if (lane == 0) S.phase[cell] = PH_INIT;
-            push(S.list[0], &S.cnt[0], cell, lane);
-            continue;
-        }
         const double ua = lane < n ? u[off + lane] : 0.0;
         const double al = lane < n ? S.alpha[off + lane] : 0.0;
         const double g = lane < n ? S.U[off + lane] - ua : 0.0;
-        const double gn2 = warp_sum(g * g), un2 = warp_sum(ua * ua);
-        if (gn2 <= kRoundoff2 * un2) {
-            // residual already at round-off: no Newton step and no polish (it would move alpha
-            // by less than its own rounding)
-            if (lane < n) S.dir[off + lane] = 0.0;
-            if (lane == 0) S.phase[cell] = PH_DONE;
-            continue;
-        }
         for (int a = lane; a < n; a += 32)
-            for (int b = 0; b <= a; ++b) {
-                const double v = S.L[(size_t)cell * npairs + tri_idx(a, b)];
-                H[a * n + b] = v;
-            }
+            for (int b = 0; b <= a; ++b) H[a * n + b] = S.L[(size_t)cell * npairs + tri_idx(a, b)];
         __syncwarp();
         const double d = warp_chol_solve<n>(H, -g, lane);
         __syncwarp();
+        const double gn2 = warp_sum(g * g), un2 = warp_sum(ua * ua);
         if (lane < n) S.dir[off + lane] = d;
         if (sqrt(gn2) <= np.tau * sqrt(un2)) {
-            if (lane == 0) S.phase[cell] = PH_DONE;
+            if (lane == 0) S.phase[cell] = PH_DONE;  // converged; d is the polish step
             continue;
         }
         const double au = warp_sum(al * ua), gd = warp_sum(g * d);
@@ -96,7 +135,8 @@ begin_kernel(Tables T, NewtonState S, const double *__restrict__ u, const double
 // ---------------------------------------------------------------------------------------------
 template <int NN, bool FILTER>
 __global__ void __launch_bounds__(kWarps * 32)
-eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np)
+eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
+            float *__restrict__ psi32)
 {
     constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2;
     __shared__ double sH[kWarps][n * n];
@@ -136,7 +176,11 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
             double z = 0.0;
 #pragma unroll
             for (int a = 0; a < n; ++a) z = fma(atv[a], Mt[a * Qp + q], z);
-            const double e = wq[q] * exp(z);
+            const double ez = kexp(z, T.exptab);
+            // the ansatz of the trial point: the last accepted trial of a closure leaves the
+            // ansatz of its solution behind, so no separate pass is needed
+            if (psi32) psi32[(size_t)cell * Qp + q] = (float)ez;
+            const double e = wq[q] * ez;
 #pragma unroll
             for (int c = 0; c < n2; ++c) V[c] = fma(e, Mt[c * Qp + q], V[c]);
         }
@@ -185,7 +229,7 @@ finish_kernel(Tables T, NewtonState S, double *__restrict__ alpha_out, double *_
 #pragma unroll
             for (int b = 0; b < n; ++b) z = fma(av[b], T.Mt[b * Qp + q], z);
             if (psi) {
-                const double e = exp(z);
+                const double e = kexp(z, T.exptab);
                 psi[(size_t)cell * Qp + q] = e;
                 if (psi32) psi32[(size_t)cell * Qp + q] = (float)e;
             } else {
@@ -217,7 +261,7 @@ moments_kernel(Tables T, const double *__restrict__ alpha, double *__restrict__ 
             double z = 0.0;
 #pragma unroll
             for (int a = 0; a < n; ++a) z = fma(av[a], T.Mt[a * Qp + q], z);
-            const double e = T.w[q] * exp(z);
+            const double e = T.w[q] * kexp(z, T.exptab);
 #pragma unroll
             for (int c = 0; c < n2; ++c) acc[c] = fma(e, T.Mt[c * Qp + q], acc[c]);
         }
@@ -265,7 +309,7 @@ __global__ void ansatz_kernel(Tables T, const double *__restrict__ alpha, double
         for (int q = lane; q < Qf; q += 32) {
             double z = 0.0;
             for (int b = 0; b < n; ++b) z = fma(alpha[(size_t)cell * n + b], T.Mt[b * Qp + q], z);
-            psi[(size_t)cell * Qf + q] = exp(z);
+            psi[(size_t)cell * Qf + q] = kexp(z, T.exptab);
         }
     }
 }
@@ -325,21 +369,31 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                  const double *u, const double *alpha_in, int first, NewtonParams np,
                  cudaStream_t s)
 {
+    (void)T;
+    int blocks = (C + 255) / 256;
+    if (blocks > mn->nsm * 8) blocks = mn->nsm * 8;
+    {
+        LaunchScope ls(mn, PK_BEGIN, s, C);
+        KITRT_DISPATCH_N(mn->N, begin_test_kernel<NN><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(S, u, alpha_in, first, np, C));
+        if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
+    }
+    if (first) return KITRT_OK;
     const int grid = grid_for(mn, C, 8);
-    LaunchScope ls(mn, PK_BEGIN, s, C);
-    KITRT_DISPATCH_N(mn->N, begin_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, S, u, alpha_in, first, np, C));
+    LaunchScope ls(mn, PK_BEGIN, s, 0);
+    KITRT_DISPATCH_N(mn->N, predict_kernel<NN><<<grid, kWarps * 32, 0, s>>>(S, u, np));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
-                     const double *u, int k, NewtonParams np, cudaStream_t s, bool filter)
+                     const double *u, int k, NewtonParams np, cudaStream_t s, bool filter,
+                     float *psi32)
 {
     const int grid = grid_for(mn, C, 4);
     LaunchScope ls(mn, PK_EVAL, s, 0);
     if (filter) {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np)));
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32)));
     } else {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np)));
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32)));
     }
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }

@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include "kitrt_internal.cuh"
+#include "kexp.cuh"
 #include "newton_common.cuh"
 
 namespace {
@@ -158,7 +159,10 @@ struct MixedDims {
     static constexpr int tcols = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);
 };
 
-// Byte layout of the dynamic shared memory of the mixed kernel.
+// Byte layout of the dynamic shared memory of the mixed kernel. Each of the two chunk buffers
+// holds the operands split into a high and a low part (x = x_hi + x_lo, both representable in
+// the tensor-core input format), so that E.M ~ E_hi.M_hi + E_hi.M_lo + E_lo.M_hi is accurate to
+// about FP32 rounding instead of the input format's.
 template <int NN, bool BF16>
 struct MixedSmem {
     static constexpr int esz = BF16 ? 2 : 4;
@@ -167,11 +171,12 @@ struct MixedSmem {
     static constexpr int SBO = (kChunk / T) * 128;               // 8-row groups
     static constexpr int A_bytes = kTileM * kChunk * esz;
     static constexpr int B_bytes = MixedDims<NN>::NP * kChunk * esz;
-    static constexpr int off_A0 = 0;
-    static constexpr int off_A1 = off_A0 + A_bytes;
-    static constexpr int off_B0 = off_A1 + A_bytes;
-    static constexpr int off_B1 = off_B0 + B_bytes;
-    static constexpr int off_V = (off_B1 + B_bytes + 1023) / 1024 * 1024;
+    static constexpr int buf_bytes = 2 * A_bytes + 2 * B_bytes;  // A_hi, A_lo, B_hi, B_lo
+    static __host__ __device__ constexpr int off_Ahi(int b) { return b * buf_bytes; }
+    static __host__ __device__ constexpr int off_Alo(int b) { return b * buf_bytes + A_bytes; }
+    static __host__ __device__ constexpr int off_Bhi(int b) { return b * buf_bytes + 2 * A_bytes; }
+    static __host__ __device__ constexpr int off_Blo(int b) { return b * buf_bytes + 2 * A_bytes + B_bytes; }
+    static constexpr int off_V = (2 * buf_bytes + 1023) / 1024 * 1024;
     static constexpr int V_bytes = kTileM * Dims<NN>::n2 * 8;
     static constexpr int off_H = off_V + V_bytes;
     static constexpr int H_bytes = kWarpsM * Dims<NN>::n * Dims<NN>::n * 8;
@@ -185,36 +190,42 @@ struct MixedSmem {
     }
 };
 
+// Work item = (tile of 128 listed cells, range of quadrature chunks). When few cells are listed
+// (the later sweeps of a closure), each tile's quadrature range is split over several CTAs so
+// that every SM gets work; the partial moments of a work item are added into Vacc (one FP64 row
+// of n2 moments per list position) with atomics, and mixed_post_kernel finishes the Newton logic.
 template <int NN, bool BF16, bool MOMENTS_ONLY>
 __global__ void __launch_bounds__(kThreads, 1)
-eval_mixed_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
-                  const void *__restrict__ Mhi, const double *__restrict__ alpha_in,
-                  double *__restrict__ Vout, int C)
+eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
+                  const double *__restrict__ alpha_in, double *__restrict__ Vacc, int C,
+                  int target_items, float *__restrict__ psi32)
 {
     using D = MixedDims<NN>;
     using L = MixedSmem<NN, BF16>;
     constexpr int n = D::n, n2 = D::n2, NP = D::NP;
     extern __shared__ __align__(1024) unsigned char smem[];
-    double *sV = (double *)(smem + L::off_V);
     uint64_t *bar = (uint64_t *)(smem + L::off_bar);
     uint32_t *tmem_slot = (uint32_t *)(smem + L::off_bar + 16);
     int *abort_flag = (int *)(smem + L::off_bar + 24);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int Qp = T.Qp, nchunks = Qp / kChunk;
 
     int cnt_in;
     const int32_t *list_in = nullptr;
-    int32_t *list_out = nullptr, *cnt_out = nullptr;
     if (MOMENTS_ONLY) {
         cnt_in = C;
     } else {
         list_in = S.list[k & 1];
-        list_out = S.list[(k + 1) & 1];
         cnt_in = S.cnt[k % 3];
-        cnt_out = &S.cnt[(k + 1) % 3];
         if (blockIdx.x == 0 && tid == 0) S.cnt[(k + 2) % 3] = 0;
     }
-    if ((int)blockIdx.x * kTileM >= cnt_in) return;  // no tile for this CTA (uniform per CTA)
+    const int tiles = (cnt_in + kTileM - 1) / kTileM;
+    int ks = tiles > 0 ? (target_items + tiles - 1) / tiles : 1;
+    ks = ks < 1 ? 1 : (ks > nchunks ? nchunks : ks);
+    const int cpp = (nchunks + ks - 1) / ks;  // chunks per part
+    ks = (nchunks + cpp - 1) / cpp;
+    const int items = tiles * ks;
+    if ((int)blockIdx.x >= items) return;  // no work item for this CTA (uniform per CTA)
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -231,7 +242,9 @@ eval_mixed_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, 
     uint32_t commits[2] = {0, 0}, waited[2] = {0, 0};
     const int r = tid & (kTileM - 1), h = tid >> 7;  // row of this thread, half of each chunk
 
-    for (int tile = blockIdx.x; tile * kTileM < cnt_in; tile += gridDim.x) {
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int tile = item / ks, part = item % ks;
+        const int c_begin = part * cpp, c_end = min(nchunks, c_begin + cpp);
         const int base = tile * kTileM;
         const int rows = min(kTileM, cnt_in - base);
         int cell = -1;
@@ -258,10 +271,10 @@ eval_mixed_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, 
                 }
             }
         }
-        for (int c = 0; c < nchunks; ++c) {
+        for (int c = c_begin; c < c_end; ++c) {
             const int b = c & 1;
-            unsigned char *A = smem + (b ? L::off_A1 : L::off_A0);
-            unsigned char *B = smem + (b ? L::off_B1 : L::off_B0);
+            unsigned char *Ahi = smem + L::off_Ahi(b), *Alo = smem + L::off_Alo(b);
+            unsigned char *Bhi = smem + L::off_Bhi(b), *Blo = smem + L::off_Blo(b);
             if (commits[b] > waited[b]) {
                 // the MMAs that read this buffer must have finished before it is overwritten:
                 // one thread waits on the buffer's mbarrier, the CTA barrier orders the rest
@@ -281,39 +294,54 @@ eval_mixed_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, 
                     double z = 0.0;
 #pragma unroll
                     for (int a = 0; a < n; ++a) z = fma(at[a], T.Mt[a * Qp + q], z);
-                    e = T.w[q] * exp(z);
+                    const double ez = kexp(z, T.exptab);
+                    // ansatz of the trial point (the last accepted trial leaves the solution's)
+                    if (psi32) psi32[(size_t)cell * Qp + q] = (float)ez;
+                    e = T.w[q] * ez;
 #pragma unroll
                     for (int a = 0; a < n; ++a) U[a] = fma(e, T.Mt[a * Qp + q], U[a]);
                 }
                 const int kk = h * (kChunk / 2) + j;
+                const float ef = (float)e;
                 if (BF16) {
-                    *(__nv_bfloat16 *)(A + L::elem_off(r, kk)) = __float2bfloat16_rn((float)e);
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(ef);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(ef - __bfloat162float(hi));
+                    *(__nv_bfloat16 *)(Ahi + L::elem_off(r, kk)) = hi;
+                    *(__nv_bfloat16 *)(Alo + L::elem_off(r, kk)) = lo;
                 } else {
-                    uint32_t t32;
-                    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t32) : "f"((float)e));
-                    *(uint32_t *)(A + L::elem_off(r, kk)) = t32;
+                    uint32_t hi, lo;
+                    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(ef));
+                    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(ef - __uint_as_float(hi)));
+                    *(uint32_t *)(Ahi + L::elem_off(r, kk)) = hi;
+                    *(uint32_t *)(Alo + L::elem_off(r, kk)) = lo;
                 }
             }
-            // stage the chunk of M_hi (row-major [NP x Qp] in global, 16-byte pieces)
+            // stage the chunk of the split table (row-major [2][NP x Qp] in global: high part,
+            // then low part), in 16-byte pieces
             constexpr int per16 = L::T;  // elements per 16 bytes
             constexpr int pieces = NP * (kChunk / per16);
-            for (int p = tid; p < pieces; p += kThreads) {
-                const int row = p / (kChunk / per16), kp = (p % (kChunk / per16)) * per16;
+            for (int p = tid; p < 2 * pieces; p += kThreads) {
+                const int part = p / pieces, pp = p % pieces;
+                const int row = pp / (kChunk / per16), kp = (pp % (kChunk / per16)) * per16;
                 const uint4 v = *(const uint4 *)((const unsigned char *)Mhi +
-                                                 ((size_t)row * Qp + c * kChunk + kp) * L::esz);
-                *(uint4 *)(B + L::elem_off(row, kp)) = v;
+                                                 (((size_t)part * NP + row) * Qp + c * kChunk + kp) * L::esz);
+                *(uint4 *)((part ? Blo : Bhi) + L::elem_off(row, kp)) = v;
             }
             fence_async_smem();
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
-                const uint64_t ad = smem_desc(smem_u32(A), L::LBO, L::SBO);
-                const uint64_t bd = smem_desc(smem_u32(B), L::LBO, L::SBO);
+                const uint64_t ahi = smem_desc(smem_u32(Ahi), L::LBO, L::SBO);
+                const uint64_t alo = smem_desc(smem_u32(Alo), L::LBO, L::SBO);
+                const uint64_t bhi = smem_desc(smem_u32(Bhi), L::LBO, L::SBO);
+                const uint64_t blo = smem_desc(smem_u32(Blo), L::LBO, L::SBO);
 #pragma unroll
                 for (int j = 0; j < kChunk / L::kmma; ++j) {
                     // each MMA covers 32 bytes of K = two core matrices = 2 * LBO bytes
                     const uint64_t step = (uint64_t)((j * 2 * L::LBO) >> 4);
-                    mma_issue<BF16>(tmem, ad + step, bd + step, idesc, (c > 0 || j > 0) ? 1u : 0u);
+                    mma_issue<BF16>(tmem, alo + step, bhi + step, idesc, (c > c_begin || j > 0) ? 1u : 0u);
+                    mma_issue<BF16>(tmem, ahi + step, blo + step, idesc, 1u);
+                    mma_issue<BF16>(tmem, ahi + step, bhi + step, idesc, 1u);
                 }
                 mma_commit(&bar[b]);
             }
@@ -334,56 +362,34 @@ eval_mixed_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, 
         __syncthreads();
         tc_fence_after();
         if (*abort_flag) break;
-        // gather the row moments: FP64 gradient part from both halves, tensor part from TMEM
-        double *Vr = sV + (size_t)r * n2;
-        if (h == 1) {
+        // partial moments of this work item into the accumulator row of its list position: the
+        // FP64 gradient moments from both halves, the tensor-core moments from TMEM (warps 0-3)
+        if (r < rows && (MOMENTS_ONLY || active)) {
+            double *row = Vacc + (size_t)(base + r) * n2;
 #pragma unroll
-            for (int a = 0; a < n; ++a) Vr[a] = U[a];
+            for (int a = 0; a < n; ++a) atomicAdd(row + a, U[a]);
         }
-        __syncthreads();
         if (h == 0) {
-#pragma unroll
-            for (int a = 0; a < n; ++a) Vr[a] += U[a];
             const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+            double *row = Vacc + (size_t)(base + r) * n2;
 #pragma unroll
             for (int c0 = 0; c0 < NP; c0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+                if (r < rows && (MOMENTS_ONLY || active)) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (c0 + i < n2 - n) Vr[n + c0 + i] = (double)v[i];
+                    for (int i = 0; i < 16; ++i)
+                        if (c0 + i < n2 - n) atomicAdd(row + n + c0 + i, (double)v[i]);
+                }
             }
         }
         tc_fence_before();
-        __syncthreads();
-        if (MOMENTS_ONLY) {
-            for (int idx = tid; idx < rows * n2; idx += kThreads) {
-                const int rr = idx / n2, cc = idx % n2;
-                Vout[(size_t)(base + rr) * n2 + cc] = sV[(size_t)rr * n2 + cc];
-            }
-        } else {
-            double *H = (double *)(smem + L::off_H) + warp * n * n;
-            for (int rr = warp; rr < rows; rr += kWarpsM) {
-                const int cl = list_in[base + rr];
-                if (S.h64[cl]) continue;
-                const int ph = S.phase[cl];
-                const double lam = ph == PH_NEWTON ? S.lam[cl] : 0.0;
-                const size_t off = (size_t)cl * n;
-                const double ua = lane < n ? u[off + lane] : 0.0;
-                const double al = lane < n ? S.alpha[off + lane] : 0.0;
-                const double di = (ph == PH_NEWTON && lane < n) ? S.dir[off + lane] : 0.0;
-                const double atl = lane < n ? (ph == PH_NEWTON ? fma(lam, di, al) : al) : 0.0;
-                newton_post<NN>(T, S, np, cl, ph, lam, atl, ua, sV + (size_t)rr * n2, H, list_out,
-                                cnt_out, lane, true);
-                __syncwarp();
-            }
-        }
         __syncthreads();
     }
     // an aborted tile may still have MMAs in flight: wait for them (bounded) before freeing TMEM
     if (tid == 0 && *abort_flag) {
         if (!MOMENTS_ONLY) atomicExch(&S.cnt[7], KITRT_ETIMEOUT);
-        else atomicExch((int *)Vout + 1, 0x7ff80000);  // poison the first moment (NaN high word)
+        else atomicExch((int *)Vacc + 1, 0x7ff80000);  // poison the first moment (NaN high word)
         for (int b = 0; b < 2; ++b)
             while (commits[b] > waited[b]) {
                 if (!mbar_wait_bounded(&bar[b], waited[b] & 1)) break;
@@ -395,9 +401,46 @@ eval_mixed_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, 
     if (warp == 0) tmem_dealloc(tmem, D::tcols);
 }
 
+// Newton logic of the listed cells after a mixed sweep: one warp per list position reads (and
+// clears) its accumulated moment row and runs the shared per-cell step.
+template <int NN>
+__global__ void __launch_bounds__(kThreads)
+mixed_post_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
+                  double *__restrict__ Vacc)
+{
+    constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2;
+    __shared__ double sH[kWarpsM][n * n];
+    __shared__ double sV[kWarpsM][n2];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int32_t *list_in = S.list[k & 1];
+    int32_t *list_out = S.list[(k + 1) & 1];
+    const int cnt_in = S.cnt[k % 3];
+    int32_t *cnt_out = &S.cnt[(k + 1) % 3];
+    for (int it = blockIdx.x * kWarpsM + wib; it < cnt_in; it += gridDim.x * kWarpsM) {
+        const int cell = list_in[it];
+        double *row = Vacc + (size_t)it * n2;
+        if (S.h64[cell]) continue;  // evaluated by the FP64 sweep (its row stays zero)
+        for (int c = lane; c < n2; c += 32) {
+            sV[wib][c] = row[c];
+            row[c] = 0.0;
+        }
+        __syncwarp();
+        const int ph = S.phase[cell];
+        const double lam = ph == PH_NEWTON ? S.lam[cell] : 0.0;
+        const size_t off = (size_t)cell * n;
+        const double ua = lane < n ? u[off + lane] : 0.0;
+        const double al = lane < n ? S.alpha[off + lane] : 0.0;
+        const double di = (ph == PH_NEWTON && lane < n) ? S.dir[off + lane] : 0.0;
+        const double at = lane < n ? (ph == PH_NEWTON ? fma(lam, di, al) : al) : 0.0;
+        newton_post<NN>(T, S, np, cell, ph, lam, at, ua, sV[wib], sH[wib], list_out, cnt_out, lane, true);
+        __syncwarp();
+    }
+}
+
 template <int NN, bool BF16, bool MO>
 int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const double *u, int k,
-                      NewtonParams np, const double *alpha_in, double *Vout, int C, cudaStream_t s)
+                      NewtonParams np, const double *alpha_in, double *Vacc, int C, cudaStream_t s,
+                      float *psi32)
 {
     using L = MixedSmem<NN, BF16>;
     static bool configured = false;
@@ -407,22 +450,33 @@ int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const
             return KITRT_ECUDA;
         configured = true;
     }
+    // persistent grid of one CTA per SM; aim at two work items per CTA
     const int tiles = (C + kTileM - 1) / kTileM;
     const int grid = tiles < mn->nsm ? (tiles > 0 ? tiles : 1) : mn->nsm;
-    eval_mixed_kernel<NN, BF16, MO><<<grid, kThreads, L::total, s>>>(
-        T, S, u, k, np, BF16 ? (const void *)mn->d_Mhi16 : (const void *)mn->d_Mhi32, alpha_in, Vout, C);
-    return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
+    const int target = 2 * mn->nsm;
+    eval_mixed_kernel<NN, BF16, MO><<<mn->nsm, kThreads, L::total, s>>>(
+        T, S, k, BF16 ? (const void *)mn->d_Mhi16 : (const void *)mn->d_Mhi32, alpha_in, Vacc, C, target,
+        psi32);
+    (void)grid;
+    if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
+    if (!MO) {
+        const int need = (C + kWarpsM - 1) / kWarpsM;
+        const int pg = need < mn->nsm * 4 ? (need > 0 ? need : 1) : mn->nsm * 4;
+        mixed_post_kernel<NN><<<pg, kThreads, 0, s>>>(T, S, u, k, np, Vacc);
+        if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
+    }
+    return KITRT_OK;
 }
 
 template <bool MO>
 int launch_mixed_dispatch(kitrt_mn *mn, const Tables &T, const NewtonState &S, const double *u, int k,
-                          NewtonParams np, const double *alpha_in, double *Vout, int C, bool bf16,
-                          cudaStream_t s)
+                          NewtonParams np, const double *alpha_in, double *Vacc, int C, bool bf16,
+                          cudaStream_t s, float *psi32)
 {
 #define MIXED_CASE(NNv)                                                                                  \
     case NNv:                                                                                            \
-        return bf16 ? launch_mixed_impl<NNv, true, MO>(mn, T, S, u, k, np, alpha_in, Vout, C, s)        \
-                    : launch_mixed_impl<NNv, false, MO>(mn, T, S, u, k, np, alpha_in, Vout, C, s);
+        return bf16 ? launch_mixed_impl<NNv, true, MO>(mn, T, S, u, k, np, alpha_in, Vacc, C, s, psi32) \
+                    : launch_mixed_impl<NNv, false, MO>(mn, T, S, u, k, np, alpha_in, Vacc, C, s, psi32);
     switch (mn->N) {
         MIXED_CASE(1)
         MIXED_CASE(2)
@@ -437,11 +491,11 @@ int launch_mixed_dispatch(kitrt_mn *mn, const Tables &T, const NewtonState &S, c
 }  // namespace
 
 int launch_eval_mixed(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u, int k,
-                      NewtonParams np, cudaStream_t s)
+                      NewtonParams np, cudaStream_t s, float *psi32)
 {
     LaunchScope ls(mn, PK_EVAL_MIXED, s, 0);
-    return launch_mixed_dispatch<false>(mn, T, S, u, k, np, nullptr, nullptr, C,
-                                        mn->p.mode == KITRT_MIXED_BF16, s);
+    return launch_mixed_dispatch<false>(mn, T, S, u, k, np, nullptr, mn->d_Vacc, C,
+                                        mn->p.mode == KITRT_MIXED_BF16, s, psi32);
 }
 
 int launch_moments_mixed(kitrt_mn *mn, const Tables &T, int C, const double *alpha, double *Vout,
@@ -450,6 +504,7 @@ int launch_moments_mixed(kitrt_mn *mn, const Tables &T, int C, const double *alp
     LaunchScope ls(mn, PK_OTHER, s, C);
     NewtonState S{};
     NewtonParams np{};
+    if (cudaMemsetAsync(Vout, 0, sizeof(double) * (size_t)C * T.n2, s) != cudaSuccess) return KITRT_ECUDA;
     return launch_mixed_dispatch<true>(mn, T, S, nullptr, 0, np, alpha, Vout, C,
-                                       mn->p.mode == KITRT_MIXED_BF16, s);
+                                       mn->p.mode == KITRT_MIXED_BF16, s, nullptr);
 }

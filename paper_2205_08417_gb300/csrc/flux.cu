@@ -1,19 +1,22 @@
 // Kinetic upwind flux of the closed ansatz and the explicit first-order update
 // [Sec. 4.4 kinetic numerical flux; Sec. 4.2 explicit iteration; Sec. 3.1 isotropic scattering].
 //
-// Cell-centric gather: one warp per cell i, lanes over the folded quadrature points. For each
-// point q the three faces contribute (w_q Omega_q . n_ik) times the upwind value (psi_iq when the
-// direction leaves the cell, psi_jq of the neighbour otherwise; the boundary ghost is psi_iq for
-// Neumann and 0 for vacuum). The per-point sum s_q is projected on the basis, F_a = sum_q m_a(q)
-// s_q, warp-reduced, and the update u <- u - dt/A F + dt R(u) is applied in place (the flux reads
-// psi only, so the in-place update is safe). psi rows are contiguous per cell, so each face
-// gather is a coalesced row segment of the neighbour.
+// Cell-centric gather: one warp per cell i, lanes over the folded quadrature points. The upwind
+// flux sum_f sum_q w_q m_q (Omega_q.n_f) psi_up is evaluated in its fluctuation form
+//     F_i = sum_f sum_{q: Omega_q.n_f < 0} w_q m_q (Omega_q.n_f) (psi_up,f,q - psi_iq),
+// which equals it exactly in exact arithmetic because the scaled normals of a closed cell sum to
+// zero (sum_f n_f = 0), so psi_iq sum_f Omega_q.n_f vanishes: outflow directions drop out, the
+// upwind value is the neighbour's psi (the ghost: psi_iq for Neumann, 0 for vacuum), and a
+// uniform state gives exactly zero flux at any working precision. F is projected on the basis,
+// warp-reduced, and u <- u - dt/A F + dt R(u) is applied in place (the flux reads psi only).
+// psi rows are contiguous per cell, so each face gather is a coalesced row segment.
 #include "kitrt_internal.cuh"
 
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 8;
+constexpr int kBatch = 16;  // cells per warp batch in the FP32 flux
 
 template <int NN, typename PsiT>
 __global__ void __launch_bounds__(kWarps * 32)
@@ -42,18 +45,15 @@ flux_update_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restr
             double s = 0.0;
             {
                 const double d = fma(wx, nx0, wy * ny0);
-                const double up = d > 0.0 ? pi : (nb.x >= 0 ? (double)psi[(size_t)nb.x * Qp + q] : ghost);
-                s = fma(d, up, s);
+                if (d < 0.0) s = fma(d, (nb.x >= 0 ? (double)psi[(size_t)nb.x * Qp + q] : ghost) - pi, s);
             }
             {
                 const double d = fma(wx, nx1, wy * ny1);
-                const double up = d > 0.0 ? pi : (nb.y >= 0 ? (double)psi[(size_t)nb.y * Qp + q] : ghost);
-                s = fma(d, up, s);
+                if (d < 0.0) s = fma(d, (nb.y >= 0 ? (double)psi[(size_t)nb.y * Qp + q] : ghost) - pi, s);
             }
             {
                 const double d = fma(wx, nx2, wy * ny2);
-                const double up = d > 0.0 ? pi : (nb.z >= 0 ? (double)psi[(size_t)nb.z * Qp + q] : ghost);
-                s = fma(d, up, s);
+                if (d < 0.0) s = fma(d, (nb.z >= 0 ? (double)psi[(size_t)nb.z * Qp + q] : ghost) - pi, s);
             }
 #pragma unroll
             for (int a = 0; a < n; ++a) F[a] = fma(T.Mt[a * Qp + q], s, F[a]);
@@ -76,8 +76,18 @@ flux_update_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restr
     }
 }
 
-// FP32 variant for the mixed modes: FP32 ansatz, FP32 upwind sums, Kahan-compensated FP32
-// projection per lane, FP64 warp reduction and update.
+// FP32 variant for the mixed modes: FP32 ansatz and upwind sums, Kahan-compensated FP32
+// projection per lane, a compensated (two-sum) FP32 butterfly across the warp, and the FP64
+// update applied afterwards with every lane busy. A warp takes a batch of kBatch consecutive cells:
+// their flux moments go to shared memory, then the warp updates all (cell, moment) pairs of the
+// batch (FP64 instructions on a partly idle warp cost as much as on a full one).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
 template <int NN>
 __global__ void __launch_bounds__(kWarps * 32)
 flux_update32_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restrict__ nrm,
@@ -87,59 +97,75 @@ flux_update32_kernel(Tables T, const int4 *__restrict__ nbr, const double *__res
                      int bc, int C)
 {
     constexpr int n = (NN + 1) * (NN + 2) / 2;
+    __shared__ double sF[kWarps][kBatch * n];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int Qp = T.Qp;
-    for (int i = blockIdx.x * kWarps + wib; i < C; i += gridDim.x * kWarps) {
-        const int4 nb = nbr[i];
-        const float nx0 = (float)nrm[6 * (size_t)i], ny0 = (float)nrm[6 * (size_t)i + 1];
-        const float nx1 = (float)nrm[6 * (size_t)i + 2], ny1 = (float)nrm[6 * (size_t)i + 3];
-        const float nx2 = (float)nrm[6 * (size_t)i + 4], ny2 = (float)nrm[6 * (size_t)i + 5];
-        const float *pi_row = psi + (size_t)i * Qp;
-        float F[n], Fc[n];
+    for (int base = (blockIdx.x * kWarps + wib) * kBatch; base < C; base += gridDim.x * kWarps * kBatch) {
+        const int nb_cells = C - base < kBatch ? C - base : kBatch;
+        for (int ci = 0; ci < nb_cells; ++ci) {
+            const int i = base + ci;
+            const int4 nb = nbr[i];
+            const float nx0 = (float)nrm[6 * (size_t)i], ny0 = (float)nrm[6 * (size_t)i + 1];
+            const float nx1 = (float)nrm[6 * (size_t)i + 2], ny1 = (float)nrm[6 * (size_t)i + 3];
+            const float nx2 = (float)nrm[6 * (size_t)i + 4], ny2 = (float)nrm[6 * (size_t)i + 5];
+            const float *pi_row = psi + (size_t)i * Qp;
+            float F[n], Fc[n];
 #pragma unroll
-        for (int a = 0; a < n; ++a) F[a] = Fc[a] = 0.0f;
-        for (int q = lane; q < Qp; q += 32) {
-            const float pi = pi_row[q];
-            const float wx = T.wox32[q], wy = T.woy32[q];
-            const float ghost = bc == 0 ? pi : 0.0f;
-            float s = 0.0f;
-            {
-                const float d = fmaf(wx, nx0, wy * ny0);
-                const float up = d > 0.0f ? pi : (nb.x >= 0 ? psi[(size_t)nb.x * Qp + q] : ghost);
-                s = fmaf(d, up, s);
+            for (int a = 0; a < n; ++a) F[a] = Fc[a] = 0.0f;
+            for (int q = lane; q < Qp; q += 32) {
+                const float pi = pi_row[q];
+                const float wx = T.wox32[q], wy = T.woy32[q];
+                const float ghost = bc == 0 ? pi : 0.0f;
+                float s = 0.0f;
+                {
+                    const float d = fmaf(wx, nx0, wy * ny0);
+                    if (d < 0.0f) s = fmaf(d, (nb.x >= 0 ? psi[(size_t)nb.x * Qp + q] : ghost) - pi, s);
+                }
+                {
+                    const float d = fmaf(wx, nx1, wy * ny1);
+                    if (d < 0.0f) s = fmaf(d, (nb.y >= 0 ? psi[(size_t)nb.y * Qp + q] : ghost) - pi, s);
+                }
+                {
+                    const float d = fmaf(wx, nx2, wy * ny2);
+                    if (d < 0.0f) s = fmaf(d, (nb.z >= 0 ? psi[(size_t)nb.z * Qp + q] : ghost) - pi, s);
+                }
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    const float y = fmaf(T.Mt32[a * Qp + q], s, -Fc[a]);
+                    const float t = F[a] + y;
+                    Fc[a] = (t - F[a]) - y;
+                    F[a] = t;
+                }
             }
-            {
-                const float d = fmaf(wx, nx1, wy * ny1);
-                const float up = d > 0.0f ? pi : (nb.y >= 0 ? psi[(size_t)nb.y * Qp + q] : ghost);
-                s = fmaf(d, up, s);
-            }
-            {
-                const float d = fmaf(wx, nx2, wy * ny2);
-                const float up = d > 0.0f ? pi : (nb.z >= 0 ? psi[(size_t)nb.z * Qp + q] : ghost);
-                s = fmaf(d, up, s);
-            }
+            // value = F - Fc per lane; butterfly with two-sum keeps the rounding errors
+            float mine_s = 0.0f, mine_e = 0.0f;
 #pragma unroll
             for (int a = 0; a < n; ++a) {
-                const float y = fmaf(T.Mt32[a * Qp + q], s, -Fc[a]);
-                const float t = F[a] + y;
-                Fc[a] = (t - F[a]) - y;
-                F[a] = t;
+                float sv = F[a], ev = -Fc[a];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float so = __shfl_xor_sync(kFull, sv, o), eo = __shfl_xor_sync(kFull, ev, o);
+                    float t, e;
+                    two_sum(sv, so, t, e);
+                    sv = t;
+                    ev = ev + eo + e;
+                }
+                if (lane == a) {
+                    mine_s = sv;
+                    mine_e = ev;
+                }
             }
+            if (lane < n) sF[wib][ci * n + lane] = (double)mine_s + (double)mine_e;
         }
-        double Fa = 0.0;
-#pragma unroll
-        for (int a = 0; a < n; ++a) {
-            double v = (double)F[a] - (double)Fc[a];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            if (lane == a) Fa = v;
+        __syncwarp();
+        for (int idx = lane; idx < nb_cells * n; idx += 32) {
+            const int ci = idx / n, a = idx - ci * n, i = base + ci;
+            const double ua = u[(size_t)i * n + a];
+            const double u0 = u[(size_t)i * n];
+            const double R = -sa[i] * ua - ss[i] * (ua - (a == 0 ? u0 : 0.0)) + qs[i] * T.mbar[a];
+            u[(size_t)i * n + a] = ua - dt / area[i] * sF[wib][idx] + dt * R;
         }
-        const double u0 = u[(size_t)i * n];
-        if (lane < n) {
-            const double ua = u[(size_t)i * n + lane];
-            const double R = -sa[i] * ua - ss[i] * (ua - (lane == 0 ? u0 : 0.0)) + qs[i] * T.mbar[lane];
-            u[(size_t)i * n + lane] = ua - dt / area[i] * Fa + dt * R;
-        }
+        __syncwarp();
     }
 }
 
@@ -153,6 +179,8 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
     int need = (C + kWarps - 1) / kWarps;
     int cap = mn->nsm * 8;
     int grid = need < cap ? (need > 0 ? need : 1) : cap;
+    const int need32 = (C + kWarps * kBatch - 1) / (kWarps * kBatch);
+    const int grid32 = need32 < cap ? (need32 > 0 ? need32 : 1) : cap;
     LaunchScope ls(mn, PK_FLUX, s, C);
 #define FLUX_CASE(NN)                                                                          \
     case NN:                                                                                   \
@@ -160,7 +188,7 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
             flux_update_kernel<NN, double><<<grid, kWarps * 32, 0, s>>>(                        \
                 T, m->d_nbr, m->d_nrm, m->d_area, psi, u, sa, ss, q, dt, bc, C);               \
         else                                                                                   \
-            flux_update32_kernel<NN><<<grid, kWarps * 32, 0, s>>>(                              \
+            flux_update32_kernel<NN><<<grid32, kWarps * 32, 0, s>>>(                            \
                 T, m->d_nbr, m->d_nrm, m->d_area, psi32, u, sa, ss, q, dt, bc, C);             \
         break;
     switch (mn->N) {

@@ -190,6 +190,7 @@ Tables kitrt_mn::tables() const
     T.w32 = d_w32;
     T.wox32 = d_wox32;
     T.woy32 = d_woy32;
+    T.exptab = d_exptab;
     return T;
 }
 
@@ -439,22 +440,36 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     std::vector<float> Mt32(Mt.begin(), Mt.end()), w32(w.begin(), w.end());
     std::vector<float> wox32(wox.begin(), wox.end()), woy32(woy.begin(), woy.end());
     // tensor-core operand of the mixed modes: the degree N+1..2N basis functions (rows n..n2-1
-    // of Mt), padded to a multiple of 16 rows, rounded to TF32 (nearest, ties away) and to BF16
-    // (nearest even)
+    // of Mt), padded to a multiple of 16 rows and split into a high and a low part in TF32
+    // (nearest, ties away) and in BF16 (nearest even): [2][NP x Qp], high part first
     const int nhi = n2 - n, NP = (nhi + 15) / 16 * 16;
-    std::vector<float> Mhi32((size_t)NP * Qp, 0.0f);
-    std::vector<unsigned short> Mhi16((size_t)NP * Qp, 0);
+    std::vector<float> Mhi32((size_t)2 * NP * Qp, 0.0f);
+    std::vector<unsigned short> Mhi16((size_t)2 * NP * Qp, 0);
+    auto tf32 = [](float f) {
+        uint32_t bits;
+        memcpy(&bits, &f, 4);
+        bits = (bits + 0x1000u) & ~0x1FFFu;
+        float r;
+        memcpy(&r, &bits, 4);
+        return r;
+    };
+    auto bf16 = [](float f, float *back) {
+        uint32_t bits;
+        memcpy(&bits, &f, 4);
+        const uint32_t rb = (bits + 0x7FFFu + ((bits >> 16) & 1u)) & 0xFFFF0000u;
+        memcpy(back, &rb, 4);
+        return (unsigned short)(rb >> 16);
+    };
     for (int c = 0; c < nhi; ++c)
         for (int q = 0; q < Qp; ++q) {
-            float f = (float)Mt[(size_t)(n + c) * Qp + q];
-            uint32_t bits;
-            memcpy(&bits, &f, 4);
-            uint32_t t = (bits + 0x1000u) & ~0x1FFFu;
-            float ft;
-            memcpy(&ft, &t, 4);
-            Mhi32[(size_t)c * Qp + q] = ft;
-            uint32_t rb = bits + 0x7FFFu + ((bits >> 16) & 1u);
-            Mhi16[(size_t)c * Qp + q] = (unsigned short)(rb >> 16);
+            const double x = Mt[(size_t)(n + c) * Qp + q];
+            const float hi = tf32((float)x);
+            Mhi32[(size_t)c * Qp + q] = hi;
+            Mhi32[((size_t)NP + c) * Qp + q] = tf32((float)(x - (double)hi));
+            float bhi;
+            Mhi16[(size_t)c * Qp + q] = bf16((float)x, &bhi);
+            float dummy;
+            Mhi16[((size_t)NP + c) * Qp + q] = bf16((float)(x - (double)bhi), &dummy);
         }
     TRY(dev_upload(mn, &mn->d_Mt, Mt));
     TRY(dev_upload(mn, &mn->d_w, w));
@@ -468,6 +483,10 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_upload(mn, &mn->d_w32, w32));
     TRY(dev_upload(mn, &mn->d_wox32, wox32));
     TRY(dev_upload(mn, &mn->d_woy32, woy32));
+    // 2^(j/256), j = 0..255, rounded to double from extended precision
+    std::vector<double> exptab(256);
+    for (int j = 0; j < 256; ++j) exptab[j] = (double)exp2l((long double)j / 256.0L);
+    TRY(dev_upload(mn, &mn->d_exptab, exptab));
     TRY(dev_upload(mn, &mn->d_Mhi32, Mhi32));
     TRY(dev_upload(mn, &mn->d_Mhi16, Mhi16));
 
@@ -489,14 +508,19 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_alloc(mn, &S.status, C));
     TRY(dev_alloc(mn, &S.list[0], C));
     TRY(dev_alloc(mn, &S.list[1], C));
-    TRY(dev_alloc(mn, &S.cnt, 8));
+    TRY(dev_alloc(mn, &S.cnt, 16));
     TRY(dev_alloc(mn, &mn->d_psi, C * Qp));
     if (p.mode != KITRT_FP64) {
         TRY(dev_alloc(mn, &mn->d_psi32, C * Qp));
+        TRY(dev_alloc(mn, &mn->d_Vacc, C * (size_t)n2));
+        if (cudaMemset(mn->d_Vacc, 0, sizeof(double) * C * (size_t)n2) != cudaSuccess) {
+            kitrt_mn_destroy(mn);
+            return KITRT_ECUDA;
+        }
         TRY(dev_alloc(mn, &S.h64, C));
         TRY(dev_alloc(mn, &S.gnorm, C));
     }
-    if (cudaMallocHost(&mn->h_cnt, 8 * sizeof(int32_t)) != cudaSuccess) {
+    if (cudaMallocHost(&mn->h_cnt, 16 * sizeof(int32_t)) != cudaSuccess) {
         kitrt_mn_destroy(mn);
         return KITRT_ENOMEM;
     }
@@ -561,12 +585,16 @@ static int polish_of(const kitrt_mn *mn) { return mn->p.polish && mn->p.mode == 
 // first); first = 0 reuses the state of the previous closure as the predictor. Leaves the
 // converged state in mn->st; returns the first failure status or KITRT_OK.
 static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, int first,
-                       cudaStream_t s, kitrt_stats *stats)
+                       cudaStream_t s, kitrt_stats *stats, float *psi32 = nullptr)
 {
     const int C = mn->mesh->C;
     const Tables T = mn->tables();
     NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, polish_of(mn)};
-    CUDA_OK(cudaMemsetAsync(mn->st.cnt, 0, 8 * sizeof(int32_t), s));
+    CUDA_OK(cudaMemsetAsync(mn->st.cnt, 0, 16 * sizeof(int32_t), s));
+    // mixed sweeps accumulate moments per list slot; every slot is cleared by its consumer, but an
+    // aborted closure could leave partial sums behind
+    if (mn->d_Vacc)
+        CUDA_OK(cudaMemsetAsync(mn->d_Vacc, 0, sizeof(double) * (size_t)C * mn->n2, s));
     int rc = launch_begin(mn, T, mn->st, C, u, alpha_in, first, np, s);
     if (rc) return rc;
     const int batch = 4;
@@ -580,8 +608,8 @@ static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, in
                 // FP64 sweep of the cells handed over in earlier rounds, then the tensor-core sweep
                 // of the others (cells it hands over now wait for the next round, so no cell is
                 // evaluated twice in one round)
-                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, true);
-                if (!rc) rc = launch_eval_mixed(mn, T, mn->st, C, u, k, np, s);
+                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, true, psi32);
+                if (!rc) rc = launch_eval_mixed(mn, T, mn->st, C, u, k, np, s, psi32);
             }
             if (rc) return rc;
         }
@@ -653,11 +681,13 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
     const Tables T = mn->tables();
     int rc = KITRT_OK;
     for (int32_t it = 0; it < nsteps; ++it) {
-        rc = run_closure(mn, u, alpha, it == 0, s, stats);
-        if (rc) break;
         const bool fp64 = mn->p.mode == KITRT_FP64;
-        rc = launch_finish(mn, T, mn->st, C, alpha, fp64 ? mn->d_psi : nullptr,
-                           fp64 ? nullptr : mn->d_psi32, polish_of(mn), it > 0, s);
+        // mixed modes: the evaluation sweeps write the FP32 ansatz of every accepted point, and
+        // with no polish step the solution's ansatz is already in place
+        rc = run_closure(mn, u, alpha, it == 0, s, stats, fp64 ? nullptr : mn->d_psi32);
+        if (rc) break;
+        rc = launch_finish(mn, T, mn->st, C, alpha, fp64 ? mn->d_psi : nullptr, nullptr,
+                           polish_of(mn), it > 0, s);
         if (rc) break;
         rc = launch_flux_update(mn, T, C, fp64 ? mn->d_psi : nullptr, fp64 ? nullptr : mn->d_psi32,
                                 u, sigma_a, sigma_s, q, dt, mn->p.bc, s);

@@ -1,0 +1,38 @@
+// FP64 exponential for the quadrature sums, by the table-driven method of P. T. P. Tang
+// ("Table-driven implementation of the exponential function in IEEE floating-point arithmetic",
+// ACM TOMS 15(2), 1989), written from the mathematics with a 256-entry table:
+//   k = nearest integer to x * 256 / ln2,  k = 256 m + j (0 <= j < 256),
+//   r = x - k ln2/256 (two-part constant, |r| <= ln2/512),
+//   exp(x) = 2^m * T_j * (1 + p(r)),  T_j = 2^(j/256) (table, correctly rounded),
+//   p(r) = r + r^2/2 + r^3/6 + r^4/24 + r^5/120 (truncation error below r^6/720 < 1e-20).
+// About ten FP64-pipe instructions; the scaling by 2^m is an integer add to the exponent field.
+// Arguments below -707 return 0 (the true value is below 1e-307, a weight no sum here can see),
+// above 709.78 return +inf, and NaN propagates.
+#pragma once
+
+namespace kitrt_dev {
+
+__device__ __forceinline__ double kexp(double x, const double *__restrict__ tab)
+{
+    const double kInvL = 369.3299304675746;           // 256 / ln2
+    const double kL1 = 0.0027076061740622863;         // ln2/256, leading part
+    const double kL2 = 9.058776616587108e-20;         // ln2/256 - kL1
+    const double kShift = 6755399441055744.0;         // 1.5 * 2^52: rounds to an integer
+    if (!(x > -707.0)) return x != x ? x : 0.0;
+    if (x > 709.78) return __longlong_as_double(0x7ff0000000000000LL);
+    const double t = fma(x, kInvL, kShift);
+    const int k = __double2loint(t);
+    const double kf = t - kShift;
+    double r = fma(-kf, kL1, x);
+    r = fma(-kf, kL2, r);
+    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(r, p, 1.0 / 6.0);
+    p = fma(r, p, 0.5);
+    p = fma(r * r, p, r);
+    const double Tj = __ldg(tab + (k & 255));
+    const double y = fma(Tj, p, Tj);
+    const long long bits = __double_as_longlong(y) + ((long long)(k >> 8) << 52);
+    return __longlong_as_double(bits);
+}
+
+}  // namespace kitrt_dev

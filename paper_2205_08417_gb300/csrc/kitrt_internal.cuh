@@ -40,6 +40,7 @@ struct Tables {
     const float *Mt32;        // [n2 x Qp] FP32 copy
     const float *w32;
     const float *wox32, *woy32;  // FP32 copies of w * Omega
+    const double *exptab;     // [256] 2^(j/256) for kexp
 };
 
 struct NewtonState {
@@ -59,8 +60,9 @@ struct NewtonState {
     int32_t *h64;      // [C] mixed modes: 1 = this cell evaluates its Hessian in FP64 (else NULL)
     double *gnorm;     // [C] mixed modes: ||g|| at the last accepted point (else NULL)
     int32_t *list[2];  // active cell lists (ping-pong)
-    int32_t *cnt;      // [8]: cnt[0..2] rotating list counters, cnt[3] failures, cnt[4] max evals,
-                       //       cnt[5] fallbacks
+    int32_t *cnt;      // [16]: cnt[0..2] rotating list counters, cnt[3] failures, cnt[4] max
+                       //   evals, cnt[5] fallbacks, cnt[6] evaluations, cnt[7] timeout status,
+                       //   cnt[8] predictor list length
 };
 
 struct NewtonParams {
@@ -93,6 +95,8 @@ struct kitrt_mn {
     unsigned short *d_Mhi16 = nullptr;   // [NP x Qp] BF16 copy
     float *d_wox32 = nullptr, *d_woy32 = nullptr;
     double *d_V = nullptr;               // [C x n2] moments scratch (kitrt_hessian)
+    double *d_Vacc = nullptr;            // [C x n2] mixed sweeps: moment accumulators per list slot
+    double *d_exptab = nullptr;          // [256] 2^(j/256)
     // workspace
     NewtonState st{};
     double *d_psi = nullptr;   // [C x Qp] FP64 ansatz
@@ -125,7 +129,7 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                  cudaStream_t s);
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s,
-                     bool filter = false);
+                     bool filter = false, float *psi32 = nullptr);
 int launch_finish(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                   double *alpha_out, double *psi, float *psi32, int polish, int compare_prev,
                   cudaStream_t s);
@@ -134,7 +138,7 @@ int launch_moments_fp64(kitrt_mn *mn, const Tables &T, int C, const double *alph
                         cudaStream_t s);
 int launch_gaunt(kitrt_mn *mn, const Tables &T, int C, const double *V, double *H, cudaStream_t s);
 int launch_eval_mixed(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u,
-                      int k, NewtonParams np, cudaStream_t s);
+                      int k, NewtonParams np, cudaStream_t s, float *psi32);
 int launch_moments_mixed(kitrt_mn *mn, const Tables &T, int C, const double *alpha, double *Vout,
                          cudaStream_t s);
 int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,

@@ -271,3 +271,29 @@ def test_d2_size_one_step_sampled_against_oracle(K):
     pos = np.searchsorted(cells, sample)
     err = np.linalg.norm(us[pos] - u_gpu[sample]) / np.linalg.norm(u_gpu[sample])
     assert err <= 1e-11, err
+
+
+def test_table_exp_against_reference_exp(K):
+    """The quadrature kernels' FP64 exp (Tang's table-driven method) against the C library's exp:
+    with alpha = (a, 0, ...) the exponent is the single rounded product a * m_0, so the ansatz
+    returned by kitrt_ansatz is exp of a known double; 1 + 2^-52 relative (about two ulps) over
+    the whole finite range, 0 below -707."""
+    m = synth.jittered_mesh(40, 0.0, 1.0, seed=0)
+    mesh = K.Mesh(m.xy, m.tri)
+    C = mesh.ncells
+    s = K.MNSolver(mesh, 1, 2)
+    w, om, M = s.quadrature()
+    m0 = M[0, 0]
+    rng = np.random.default_rng(7)
+    a0 = np.concatenate([rng.uniform(-700, 700, C - 6) / m0,
+                         np.array([0.0, 1e-300, -1e-12, 709.7, -706.9, -720.0]) / m0])
+    alpha = np.zeros((C, s.n))
+    alpha[:, 0] = a0
+    psi = s.ansatz(dev(alpha)).cpu().numpy()
+    z = a0 * m0
+    ref = np.exp(z)
+    live = z > -707
+    rel = np.abs(psi[live, 0] - ref[live]) / ref[live]
+    assert rel.max() <= 2.0 ** -51, rel.max()
+    assert (psi[~live, 0] == 0).all()
+    assert np.all(psi == psi[:, :1])  # m_0 is constant: every point sees the same exponent

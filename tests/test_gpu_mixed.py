@@ -1,8 +1,9 @@
 """GPU parity of the mixed-precision paths (tensor-core Hessian moments in TF32 or BF16, FP64
 gradient / Cholesky / line search, FP32 ansatz and flux) against the CPU oracle, through the C ABI.
 
-Bars: the Hessian within the input rounding of its tensor-core operands (TF32 2^-11, BF16 2^-8
-relative per operand, accumulated in FP32); the closure to the same tolerance as FP64 (its
+Bars: the Hessian within FP32 accumulation error (the tensor-core operands are split into high
+and low parts, so TF32 keeps about 21 and BF16 about 16 significant bits of each product, summed
+over several hundred points in FP32); the closure to the same tolerance as FP64 (its
 gradient and test are FP64); the step within 1e-5 relative L2 on the zeroth moment."""
 import math
 
@@ -44,7 +45,7 @@ def vmf_u(T, count, seed, kappa_hi=20.0):
     return (psi * scale[:, None]) @ (T.w[:, None] * T.M)
 
 
-@pytest.mark.parametrize("mode,tol", [("fp64", 1e-13), ("mixed_tf32", 3e-3), ("mixed_bf16", 2.5e-2)])
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-13), ("mixed_tf32", 1e-5), ("mixed_bf16", 1e-4)])
 @pytest.mark.parametrize("N,order", [(1, 4), (2, 10), (3, 20), (5, 30)])
 def test_hessian_matches_definition(K, mode, tol, N, order):
     """H = <m m^T exp(alpha.m)> on the oracle's full rule vs the library (FP64, or tensor-core
@@ -97,9 +98,11 @@ def test_mixed_closure_matches_oracle(K, mode, N, order):
         assert np.linalg.norm(a_gpu[i] - a_or[i]) <= bound
 
 
+@pytest.mark.parametrize("tau", [1e-10, 1e-8])
 @pytest.mark.parametrize("mode", MIXED)
-def test_mixed_line_source_m2_matches_oracle(K, mode):
-    """M_2 line source (3872 triangles, order 10), 50 steps: mixed vs the FP64 oracle on u_0."""
+def test_mixed_line_source_m2_matches_oracle(K, mode, tau):
+    """M_2 line source (3872 triangles, order 10), 50 steps: mixed vs the FP64 oracle on u_0, at
+    the FP64 Newton tolerance and at the tolerance the benchmark uses for the mixed modes."""
     m = synth.jittered_mesh(45, -1.5, 1.5, seed=1)
     mesh = K.Mesh(m.xy, m.tri)
     G = O.Geometry(m.xy, m.tri)
@@ -111,7 +114,7 @@ def test_mixed_line_source_m2_matches_oracle(K, mode):
     u_or = u0.copy()
     a_or = O.isotropic_alpha(T, u_or)
     assert O.mn_run(T, G, u_or, a_or, sa, ss, q, dt, 50)[0] == 0
-    s = K.MNSolver(mesh, 2, 10, mode=mode)
+    s = K.MNSolver(mesh, 2, 10, mode=mode, tau=tau)
     ud = dev(u0)
     ad = s.isotropic_alpha(ud)
     s.step(ud, ad, dev(sa), dev(ss), dev(q), dt=dt, nsteps=50)
@@ -157,7 +160,7 @@ def test_mixed_d2_size_sampled_against_oracle(K, mode):
     C = G.C
     dt = G.cfl_dt(0.4)
     sa, ss, q = np.zeros(C), np.ones(C), np.zeros(C)
-    s = K.MNSolver(mesh, 3, 20, mode=mode)
+    s = K.MNSolver(mesh, 3, 20, mode=mode, tau=1e-8)
     ud = dev(u0)
     ad = s.isotropic_alpha(ud)
     s.step(ud, ad, dev(sa), dev(ss), dev(q), dt=dt, nsteps=3)
