@@ -42,7 +42,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", default="mixed_tf32", help="headline closure mode")
-    ap.add_argument("--compare", default="fp64,mixed_bf16", help="comma list of extra modes to time")
+    ap.add_argument("--compare", default="fp64,mixed_bf16,learned", help="comma list of extra modes to time")
+    ap.add_argument("--train-samples", type=int, default=2_000_000,
+                    help="training moment vectors of the learned closure")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synth.WORKLOADS key (the default is the benchmarked configuration)")
@@ -175,9 +177,29 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True):
+def train_network(K, torch, W, samples, seed=4):
+    """Learned closure for this workload's basis: training data from vMF mixtures closed by the
+    FP64 Newton solver, trained with the library's MLP kernels (untimed set-up)."""
+    from paper_2205_08417_gb300 import learned
+    mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
+    s = K.MNSolver(mesh, W["N"], W["order"], mode="fp64", tau=1e-12)
+    t0 = time.perf_counter()
+    u, a = learned.training_data(s, samples, seed=seed)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = learned.train(u, a, batch=4096 if samples > 500_000 else 1024, epochs=20 if samples > 500_000 else 30)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    net.info = {"samples": net.samples, "requested": samples, "data_s": t1 - t0, "train_s": t2 - t1,
+                "final_loss": net.losses[-1], "first_loss": net.losses[0]}
+    return net
+
+
+def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None):
     mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
     s = K.MNSolver(mesh, W["N"], W["order"], mode=mode, tau=tau)
+    if net is not None:
+        s.set_mlp(net.params, net.norm)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     u = d(W["u0"])
     alpha = s.isotropic_alpha(u)
@@ -265,13 +287,15 @@ def main():
     peak = fp64_peak_tflops(torch)
     results = {}
     clocks = None
+    net = train_network(K, torch, W, args.train_samples) if "learned" in modes else None
     for mode in modes:
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         cs = ClockSampler(local) if mode == args.mode else None
         tau = args.tau if mode == "fp64" else args.tau_mixed
-        r = run_mode(K, torch, W, mode, args.steps, args.warmup, args.t_start, tau, e2e=not args.no_e2e)
+        r = run_mode(K, torch, W, mode, args.steps, args.warmup, args.t_start, tau, e2e=not args.no_e2e,
+                     net=net if mode == "learned" else None)
         r["tau"] = tau
         if cs is not None:
             clocks = cs.stop()
@@ -337,7 +361,9 @@ def main():
         "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
                         "share": v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in head["prof"].values()))}
                     for k, v in head["prof"].items()},
+        "learned_training": None if net is None else net.info,
         "modes": {m: {"cell_updates_per_s": C * args.steps / (r["ms"] / 1e3), "tau": r["tau"],
+                      "fallbacks_per_cell_step": r["stats"]["fallbacks"] / (C * args.steps),
                       "ms_per_step": r["ms"] / args.steps,
                       "evaluations_per_cell_step": r["stats"]["evaluations"] / (C * args.steps)}
                   for m, r in results.items()},

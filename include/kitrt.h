@@ -175,6 +175,12 @@ int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *sta
  * The first call allocates a [C x (2N+1)(2N+2)/2] moments buffer owned by the solver. */
 int32_t kitrt_hessian(kitrt_mn *mn, const double *alpha, double *H, void *stream);
 
+/* kitrt_closure for the first `ncells` rows only (ncells <= the mesh's cell count): closes any
+ * batch of moment vectors that fits the solver's workspace, e.g. training data for the learned
+ * closure. Same arguments and behaviour as kitrt_closure otherwise. */
+int32_t kitrt_closure_batch(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
+                            int32_t ncells, void *stream, kitrt_stats *stats);
+
 /* The closed ansatz at the folded quadrature points: psi [C x Q'] FP64 device,
  * psi_cq = exp(alpha_c . m_q). */
 int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *stream);
@@ -215,6 +221,42 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
  * threads) race on it. Synchronises with `stream` like kitrt_closure. */
 int32_t kitrt_closure_noalloc(const kitrt_mn *mn, const double *u, double *alpha,
                               int32_t *status, int32_t ncells, void *stream);
+
+/* ---- Learned closure [Sec. 3.1: neural entropy closures replace the Newton solve] --------------
+ * A plain MLP with three softplus hidden layers maps the normalised moments v = u_{1..n-1}/u_0
+ * (standardised) to alpha_{1..n-1} of the normalised problem (also standardised). Parameters are
+ * FP32, packed W1[din x H] b1[H] W2[H x H] b2[H] W3[H x H] b3[H] W4[H x dout] b4[dout]
+ * (row-major [in x out]). Training runs on the library's own kernels; all pointers are device
+ * memory and calls are asynchronous on `stream`. */
+
+/* Number of packed parameters. */
+int32_t kitrt_mlp_param_count(int32_t din, int32_t hidden, int32_t dout);
+/* Floats of caller-provided workspace that kitrt_mlp_forward / kitrt_mlp_loss_grad need for a
+ * batch of B rows: B (8 hidden + 2 dout). */
+int32_t kitrt_mlp_work_floats(int32_t B, int32_t hidden, int32_t dout);
+/* Y [B x dout] = network(X [B x din]) in FP32. */
+int32_t kitrt_mlp_forward(int32_t din, int32_t hidden, int32_t dout, const float *params,
+                          const float *X, float *Y, int32_t B, float *work, void *stream);
+/* Mean-squared loss 1/(2B) sum ||Y - T||^2 into *loss (device float) and its gradient with
+ * respect to the packed parameters into grad [param_count] (both overwritten). */
+int32_t kitrt_mlp_loss_grad(int32_t din, int32_t hidden, int32_t dout, const float *params,
+                            const float *X, const float *T, int32_t B, float *grad, float *loss,
+                            float *work, void *stream);
+/* One Adam step (Kingma & Ba) at step count t >= 1 over P parameters; m and v are the moment
+ * buffers (zero before the first step). */
+int32_t kitrt_mlp_adam(int32_t P, float *params, const float *grad, float *m, float *v, int32_t t,
+                       float lr, float beta1, float beta2, float eps, void *stream);
+/* Attach a trained network to a KITRT_LEARNED solver (hidden must be 64, din = dout = nmom - 1):
+ * params FP32 as above (converted to BF16 for inference), norm [4 (nmom-1)] FP32 =
+ * (feature means, feature scales, output means, output scales). Allocates its copy on first use. */
+int32_t kitrt_mn_set_mlp(kitrt_mn *mn, const float *params, const float *norm, int32_t hidden,
+                         void *stream);
+/* Moments u [count x nmom] (FP64) of mixtures of von Mises-Fisher densities on S^2 integrated
+ * with the solver's quadrature: centres [count x lobes x 3] (unit vectors, (x, y, mu) order),
+ * kappa and weight [count x lobes] (weight 0 = unused lobe). Training data for the network. */
+int32_t kitrt_vmf_moments(kitrt_mn *mn, const double *centres, const double *kappa,
+                          const double *weight, int32_t lobes, int32_t count, double *u,
+                          void *stream);
 
 /* Tracing: on != 0 resets the trace and records a pair of CUDA events on the launching stream
  * around every kernel the solver launches from then on; on == 0 stops recording. */

@@ -48,7 +48,7 @@ __device__ __forceinline__ void push_if(int32_t *list, int32_t *cnt, int cell, b
 template <int NN>
 __global__ void __launch_bounds__(256)
 begin_test_kernel(NewtonState S, const double *__restrict__ u, const double *__restrict__ alpha_in,
-                  int first, NewtonParams np, int C)
+                  int first, NewtonParams np, int C, int learned)
 {
     constexpr int n = Dims<NN>::n;
     for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < C; cell += gridDim.x * blockDim.x) {
@@ -64,7 +64,9 @@ begin_test_kernel(NewtonState S, const double *__restrict__ u, const double *__r
 #pragma unroll
             for (int a = 0; a < n; ++a) S.alpha[off + a] = alpha_in[off + a];
             S.phase[cell] = PH_INIT;
-            to_eval = true;
+            // learned closures go to the network first (the predictor list doubles as its list)
+            to_eval = !learned;
+            to_predict = learned;
         } else {
             double gn2 = 0.0, un2 = 0.0;
 #pragma unroll
@@ -367,17 +369,17 @@ int launch_ansatz(const Tables &T, int C, const double *alpha, double *psi, cuda
 
 int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                  const double *u, const double *alpha_in, int first, NewtonParams np,
-                 cudaStream_t s)
+                 cudaStream_t s, int learned)
 {
     (void)T;
     int blocks = (C + 255) / 256;
     if (blocks > mn->nsm * 8) blocks = mn->nsm * 8;
     {
         LaunchScope ls(mn, PK_BEGIN, s, C);
-        KITRT_DISPATCH_N(mn->N, begin_test_kernel<NN><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(S, u, alpha_in, first, np, C));
+        KITRT_DISPATCH_N(mn->N, begin_test_kernel<NN><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(S, u, alpha_in, first, np, C, learned));
         if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
     }
-    if (first) return KITRT_OK;
+    if (first || learned) return KITRT_OK;
     const int grid = grid_for(mn, C, 8);
     LaunchScope ls(mn, PK_BEGIN, s, 0);
     KITRT_DISPATCH_N(mn->N, predict_kernel<NN><<<grid, kWarps * 32, 0, s>>>(S, u, np));

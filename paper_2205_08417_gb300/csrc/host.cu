@@ -513,6 +513,7 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     if (p.mode != KITRT_FP64) {
         TRY(dev_alloc(mn, &mn->d_psi32, C * Qp));
         TRY(dev_alloc(mn, &mn->d_Vacc, C * (size_t)n2));
+        if (p.mode == KITRT_LEARNED) TRY(dev_alloc(mn, &mn->d_alpha_nn, C * (size_t)n));
         if (cudaMemset(mn->d_Vacc, 0, sizeof(double) * C * (size_t)n2) != cudaSuccess) {
             kitrt_mn_destroy(mn);
             return KITRT_ECUDA;
@@ -581,22 +582,30 @@ int32_t kitrt_isotropic_alpha(kitrt_mn *mn, const double *u, double *alpha, void
 // is applied in FP64 mode only.
 static int polish_of(const kitrt_mn *mn) { return mn->p.polish && mn->p.mode == KITRT_FP64; }
 
-// Runs the closure of every cell to completion. first = 1 starts from alpha_in (evaluation
-// first); first = 0 reuses the state of the previous closure as the predictor. Leaves the
-// converged state in mn->st; returns the first failure status or KITRT_OK.
-static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, int first,
+// Runs the closure of cells 0..C-1 to completion. first = 1 starts from alpha_in (evaluation
+// first); first = 0 reuses the state of the previous closure as the predictor. In the learned
+// mode the network proposes alpha for every cell that needs a closure, and only the cells whose
+// FP64 residual test fails enter the Newton sweeps. Leaves the converged state in mn->st; returns
+// the first failure status or KITRT_OK.
+static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha_in, int first,
                        cudaStream_t s, kitrt_stats *stats, float *psi32 = nullptr)
 {
-    const int C = mn->mesh->C;
     const Tables T = mn->tables();
     NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, polish_of(mn)};
+    const bool learned = mn->p.mode == KITRT_LEARNED;
+    if (learned && !mn->has_mlp) return KITRT_EINVAL;
     CUDA_OK(cudaMemsetAsync(mn->st.cnt, 0, 16 * sizeof(int32_t), s));
     // mixed sweeps accumulate moments per list slot; every slot is cleared by its consumer, but an
     // aborted closure could leave partial sums behind
     if (mn->d_Vacc)
         CUDA_OK(cudaMemsetAsync(mn->d_Vacc, 0, sizeof(double) * (size_t)C * mn->n2, s));
-    int rc = launch_begin(mn, T, mn->st, C, u, alpha_in, first, np, s);
+    int rc = launch_begin(mn, T, mn->st, C, u, alpha_in, first, np, s, learned);
     if (rc) return rc;
+    if (learned) {
+        rc = launch_mlp_infer(mn, u, mn->st.list[1], mn->st.cnt + 8, C, mn->d_alpha_nn, s);
+        if (!rc) rc = launch_learned_pass(mn, T, mn->st, C, u, psi32, first, s);
+        if (rc) return rc;
+    }
     const int batch = 4;
     const int max_launch = (mn->p.max_iter + 1) * (mn->p.max_halvings + 1) + 1;
     int k = 0;
@@ -626,6 +635,7 @@ static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, in
         stats->evaluations += mn->h_cnt[6];
         stats->max_evals = std::max(stats->max_evals, mn->h_cnt[4]);
         stats->failed = mn->h_cnt[3];
+        stats->fallbacks += mn->h_cnt[5];
     }
     if (mn->h_cnt[3] > 0) {
         // report the first failing code
@@ -639,24 +649,32 @@ static int run_closure(kitrt_mn *mn, const double *u, const double *alpha_in, in
 
 extern "C" {
 
-int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
-                      void *stream, kitrt_stats *stats)
+int32_t kitrt_closure_batch(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
+                            int32_t ncells, void *stream, kitrt_stats *stats)
 {
-    if (!mn || !u || !alpha) return KITRT_EINVAL;
+    if (!mn || !u || !alpha || ncells < 0 || ncells > mn->mesh->C) return KITRT_EINVAL;
+    if (ncells == 0) return KITRT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     if (stats) memset(stats, 0, sizeof(*stats));
     const int64_t launches0 = mn->launch_count;
-    int rc = run_closure(mn, u, alpha, 1, s, stats);
-    int rc2 = launch_finish(mn, mn->tables(), mn->st, mn->mesh->C, alpha, nullptr, nullptr,
+    int rc = run_closure(mn, ncells, u, alpha, 1, s, stats);
+    int rc2 = launch_finish(mn, mn->tables(), mn->st, ncells, alpha, nullptr, nullptr,
                             polish_of(mn), 0, s);
     if (status)
-        CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * mn->mesh->C,
+        CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * ncells,
                                 cudaMemcpyDeviceToDevice, s));
     if (stats) {
         stats->launches = mn->launch_count - launches0;
         CUDA_OK(cudaStreamSynchronize(s));
     }
     return rc ? rc : rc2;
+}
+
+int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
+                      void *stream, kitrt_stats *stats)
+{
+    if (!mn) return KITRT_EINVAL;
+    return kitrt_closure_batch(mn, u, alpha, status, mn->mesh->C, stream, stats);
 }
 
 int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *stream)
@@ -684,7 +702,7 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
         const bool fp64 = mn->p.mode == KITRT_FP64;
         // mixed modes: the evaluation sweeps write the FP32 ansatz of every accepted point, and
         // with no polish step the solution's ansatz is already in place
-        rc = run_closure(mn, u, alpha, it == 0, s, stats, fp64 ? nullptr : mn->d_psi32);
+        rc = run_closure(mn, C, u, alpha, it == 0, s, stats, fp64 ? nullptr : mn->d_psi32);
         if (rc) break;
         rc = launch_finish(mn, T, mn->st, C, alpha, fp64 ? mn->d_psi : nullptr, nullptr,
                            polish_of(mn), it > 0, s);

@@ -97,6 +97,10 @@ struct kitrt_mn {
     double *d_V = nullptr;               // [C x n2] moments scratch (kitrt_hessian)
     double *d_Vacc = nullptr;            // [C x n2] mixed sweeps: moment accumulators per list slot
     double *d_exptab = nullptr;          // [256] 2^(j/256)
+    void *d_mlp16 = nullptr;             // learned closure: BF16 network parameters
+    float *d_mlp_norm = nullptr;         // [4 (n-1)] feature and output means / scales
+    bool has_mlp = false;
+    double *d_alpha_nn = nullptr;        // [C x n] network proposals (learned mode)
     // workspace
     NewtonState st{};
     double *d_psi = nullptr;   // [C x Qp] FP64 ansatz
@@ -126,7 +130,11 @@ struct LaunchScope {
 int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cudaStream_t s);
 int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                  const double *u, const double *alpha_in, int first, NewtonParams np,
-                 cudaStream_t s);
+                 cudaStream_t s, int learned = 0);
+int launch_mlp_infer(kitrt_mn *mn, const double *u, const int32_t *list, const int32_t *cnt, int C,
+                     double *alpha, cudaStream_t s);
+int launch_learned_pass(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u,
+                        float *psi32, int first, cudaStream_t s);
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s,
                      bool filter = false, float *psi32 = nullptr);

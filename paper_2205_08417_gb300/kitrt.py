@@ -73,10 +73,21 @@ SIGNATURES = {
     "kitrt_mn_quadrature": (C.c_int32, [_vp, _dp, _dp, _dp]),
     "kitrt_isotropic_alpha": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_closure": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Stats)]),
+    "kitrt_closure_batch": (C.c_int32, [_vp, _vp, _vp, _vp, C.c_int32, _vp, C.POINTER(Stats)]),
     "kitrt_hessian": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_ansatz": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_step": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int32, _vp, _vp,
                                C.POINTER(Stats)]),
+    "kitrt_mlp_param_count": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32]),
+    "kitrt_mlp_work_floats": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32]),
+    "kitrt_mlp_forward": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_int32,
+                                      _vp, _vp]),
+    "kitrt_mlp_loss_grad": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_int32,
+                                        _vp, _vp, _vp, _vp]),
+    "kitrt_mlp_adam": (C.c_int32, [C.c_int32, _vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.c_float,
+                                   C.c_float, C.c_float, _vp]),
+    "kitrt_mn_set_mlp": (C.c_int32, [_vp, _vp, _vp, C.c_int32, _vp]),
+    "kitrt_vmf_moments": (C.c_int32, [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp]),
     "kitrt_closure_noalloc": (C.c_int32, [_vp, _vp, _vp, _vp, C.c_int32, _vp]),
     "kitrt_profile_enable": (C.c_int32, [_vp, C.c_int32]),
     "kitrt_profile_read": (C.c_int32, [_vp, C.POINTER(ProfileEntry), C.c_int32, _ip]),
@@ -222,6 +233,33 @@ class MNSolver:
             _check(rc, "kitrt_closure")
         return (rc, st.as_dict()) if stats else rc
 
+    def closure_batch(self, u, alpha, status=None, stats: bool = False, check: bool = True):
+        """Closure of the first u.shape[0] rows (at most the mesh's cell count)."""
+        import torch
+        st = Stats()
+        rc = _lib().kitrt_closure_batch(self.handle, _dev(u, torch.float64), _dev(alpha, torch.float64),
+                                        _dev(status, torch.int32), int(u.shape[0]), _stream(),
+                                        C.byref(st) if stats else None)
+        if check:
+            _check(rc, "kitrt_closure_batch")
+        return (rc, st.as_dict()) if stats else rc
+
+    def vmf_moments(self, centres, kappa, weight):
+        """Moments of von Mises-Fisher mixtures (device FP64 tensors [count, lobes, 3],
+        [count, lobes], [count, lobes]) on this solver's quadrature."""
+        import torch
+        count, lobes = kappa.shape
+        u = torch.empty((count, self.n), dtype=torch.float64, device=kappa.device)
+        _check(_lib().kitrt_vmf_moments(self.handle, _dev(centres, torch.float64), _dev(kappa, torch.float64),
+                                        _dev(weight, torch.float64), int(lobes), int(count), _dev(u),
+                                        _stream()), "kitrt_vmf_moments")
+        return u
+
+    def set_mlp(self, params, norm, hidden: int = 64):
+        import torch
+        _check(_lib().kitrt_mn_set_mlp(self.handle, _dev(params, torch.float32), _dev(norm, torch.float32),
+                                       int(hidden), _stream()), "kitrt_mn_set_mlp")
+
     def closure_noalloc(self, u, alpha, status=None, check: bool = True):
         """Closure of a batch (any number of rows up to the fixed scratch limit) through the
         allocation-free entry point."""
@@ -281,3 +319,40 @@ class MNSolver:
             self.close()
         except Exception:
             pass
+
+
+# ---- MLP kernels of the learned closure -------------------------------------------------------
+def mlp_param_count(din: int, hidden: int, dout: int) -> int:
+    return int(_lib().kitrt_mlp_param_count(din, hidden, dout))
+
+
+def mlp_forward(params, X, din: int, hidden: int, dout: int):
+    import torch
+    B = X.shape[0]
+    Y = torch.empty((B, dout), dtype=torch.float32, device=X.device)
+    work = torch.empty(max(1, _lib().kitrt_mlp_work_floats(B, hidden, dout)), dtype=torch.float32,
+                       device=X.device)
+    _check(_lib().kitrt_mlp_forward(din, hidden, dout, _dev(params, torch.float32), _dev(X, torch.float32),
+                                    _dev(Y), B, _dev(work), _stream()), "kitrt_mlp_forward")
+    return Y
+
+
+def mlp_loss_grad(params, X, T, din: int, hidden: int, dout: int, work=None):
+    import torch
+    B = X.shape[0]
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    if work is None:
+        work = torch.empty(_lib().kitrt_mlp_work_floats(B, hidden, dout), dtype=torch.float32,
+                           device=X.device)
+    _check(_lib().kitrt_mlp_loss_grad(din, hidden, dout, _dev(params, torch.float32), _dev(X, torch.float32),
+                                      _dev(T, torch.float32), B, _dev(grad), _dev(loss), _dev(work),
+                                      _stream()), "kitrt_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_adam(params, grad, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    import torch
+    _check(_lib().kitrt_mlp_adam(int(params.numel()), _dev(params, torch.float32), _dev(grad, torch.float32),
+                                 _dev(m, torch.float32), _dev(v, torch.float32), int(t), float(lr), float(b1),
+                                 float(b2), float(eps), _stream()), "kitrt_mlp_adam")
