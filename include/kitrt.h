@@ -222,6 +222,27 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
 int32_t kitrt_closure_noalloc(const kitrt_mn *mn, const double *u, double *alpha,
                               int32_t *status, int32_t ncells, void *stream);
 
+/* Discrete adjoint of nsteps FP64 steps (solver in KITRT_FP64 mode): the objective
+ *   J = sum_{s=0}^{nsteps-1} dt sum_{i in target} A_i sigma_a,i u^s_i0 / m_0
+ * (absorbed energy in the target cells; u_0/m_0 is the scalar flux <psi>) and its gradient with
+ * respect to per-block absorption and scattering coefficients, by the exact transpose of the step
+ * map (transposed upwind flux; closure derivative d alpha/d u = H^-1 from the implicit-function
+ * theorem; source transpose). Not a construct of the paper: it differentiates the paper's step.
+ *   u0, alpha0       device [C x n]: initial state and closure warm start (read only).
+ *   sigma_a, sigma_s, q  device [C] per-cell coefficients (sigma_a,i = the value of its block).
+ *   block_of_cell    device [C] int32 in [0, nblocks).
+ *   target           device [C] uint8 (1 = cell in the target region).
+ *   dt               time step (<= 0: cfl * min 2A/P); nsteps steps; ckpt_every >= 1 steps per
+ *                    checkpoint segment (states are recomputed forward inside a segment).
+ *   J                device [1]; dJ_dsa, dJ_dss device [nblocks] (overwritten).
+ * Allocates checkpoint and segment buffers on the device for the duration of the call (about
+ * (nsteps/ckpt_every + 2 ckpt_every + 4) C n doubles + C Q' doubles) and synchronises with
+ * `stream` before returning. */
+int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *alpha0, const double *sigma_a,
+                      const double *sigma_s, const double *q, const int32_t *block_of_cell,
+                      int32_t nblocks, const uint8_t *target, double dt, int32_t nsteps,
+                      int32_t ckpt_every, double *J, double *dJ_dsa, double *dJ_dss, void *stream);
+
 /* ---- Learned closure [Sec. 3.1: neural entropy closures replace the Newton solve] --------------
  * A plain MLP with three softplus hidden layers maps the normalised moments v = u_{1..n-1}/u_0
  * (standardised) to alpha_{1..n-1} of the normalised problem (also standardised). Parameters are

@@ -649,6 +649,24 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
 
 extern "C" {
 
+}  // extern "C"
+
+// One FP64 step on device buffers without statistics (used by the adjoint): closure of u (from
+// alpha when first, else from the previous closure's state), final alpha into `alpha`, ansatz,
+// flux and update of u.
+int kitrt_internal_step(kitrt_mn *mn, double *u, double *alpha, const double *sa, const double *ss,
+                        const double *q, double dt, int first, cudaStream_t s)
+{
+    const int C = mn->mesh->C;
+    int rc = run_closure(mn, C, u, alpha, first, s, nullptr);
+    if (rc) return rc;
+    rc = launch_finish(mn, mn->tables(), mn->st, C, alpha, mn->d_psi, nullptr, polish_of(mn), !first, s);
+    if (rc) return rc;
+    return launch_flux_update(mn, mn->tables(), C, mn->d_psi, nullptr, u, sa, ss, q, dt, mn->p.bc, s);
+}
+
+extern "C" {
+
 int32_t kitrt_closure_batch(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
                             int32_t ncells, void *stream, kitrt_stats *stats)
 {

@@ -78,6 +78,8 @@ SIGNATURES = {
     "kitrt_ansatz": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_step": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int32, _vp, _vp,
                                C.POINTER(Stats)]),
+    "kitrt_adjoint": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, _vp, C.c_double,
+                                  C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
     "kitrt_mlp_param_count": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32]),
     "kitrt_mlp_work_floats": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32]),
     "kitrt_mlp_forward": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_int32,
@@ -254,6 +256,20 @@ class MNSolver:
                                         _dev(weight, torch.float64), int(lobes), int(count), _dev(u),
                                         _stream()), "kitrt_vmf_moments")
         return u
+
+    def adjoint(self, u0, alpha0, sigma_a, sigma_s, q, block_of_cell, nblocks, target, dt, nsteps,
+                ckpt_every=16):
+        """(J, dJ/dsigma_a per block, dJ/dsigma_s per block) as device FP64 tensors."""
+        import torch
+        J = torch.empty(1, dtype=torch.float64, device=u0.device)
+        gsa = torch.empty(nblocks, dtype=torch.float64, device=u0.device)
+        gss = torch.empty(nblocks, dtype=torch.float64, device=u0.device)
+        _check(_lib().kitrt_adjoint(self.handle, _dev(u0, torch.float64), _dev(alpha0, torch.float64),
+                                    _dev(sigma_a, torch.float64), _dev(sigma_s, torch.float64),
+                                    _dev(q, torch.float64), _dev(block_of_cell, torch.int32), int(nblocks),
+                                    _dev(target, torch.uint8), float(dt), int(nsteps), int(ckpt_every),
+                                    _dev(J), _dev(gsa), _dev(gss), _stream()), "kitrt_adjoint")
+        return J, gsa, gss
 
     def set_mlp(self, params, norm, hidden: int = 64):
         import torch
