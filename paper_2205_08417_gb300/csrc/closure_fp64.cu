@@ -135,10 +135,12 @@ predict_kernel(NewtonState S, const double *__restrict__ u, NewtonParams np)
 // Armijo decision, and on acceptance the Hessian, its Cholesky factor, the convergence test and
 // the next Newton direction.
 // ---------------------------------------------------------------------------------------------
-template <int NN, bool FILTER>
+// FUSED: the warp also runs the per-cell Newton logic (used by the allocation-free closure);
+// otherwise the sweep writes the cell's moment row to Vacc[list slot] for post_thread_kernel.
+template <int NN, bool FILTER, bool FUSED>
 __global__ void __launch_bounds__(kWarps * 32)
 eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
-            float *__restrict__ psi32)
+            float *__restrict__ psi32, double *__restrict__ Vacc)
 {
     constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2;
     __shared__ double sH[kWarps][n * n];
@@ -188,6 +190,12 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
         }
 #pragma unroll
         for (int c = 0; c < n2; ++c) V[c] = warp_sum(V[c]);
+        if (!FUSED) {
+#pragma unroll
+            for (int c = 0; c < n2; ++c)
+                if (lane == (c & 31)) Vacc[(size_t)it * n2 + c] = V[c];
+            continue;
+        }
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < n2; ++c)
@@ -342,6 +350,17 @@ int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cud
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
+int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u, int k,
+                NewtonParams np, double *Vacc, cudaStream_t s)
+{
+    int blocks = (C + 255) / 256;
+    if (blocks > mn->nsm * 8) blocks = mn->nsm * 8;
+    LaunchScope ls(mn, PK_POST, s, 0);
+    const int mixed = mn->p.mode != KITRT_FP64;
+    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(T, S, u, k, np, Vacc, mixed));
+    return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
+}
+
 int launch_moments_fp64(kitrt_mn *mn, const Tables &T, int C, const double *alpha, double *V, cudaStream_t s)
 {
     const int grid = grid_for(mn, C, 8);
@@ -388,14 +407,16 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
 
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s, bool filter,
-                     float *psi32)
+                     float *psi32, double *Vacc)
 {
     const int grid = grid_for(mn, C, 4);
     LaunchScope ls(mn, PK_EVAL, s, 0);
-    if (filter) {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32)));
+    if (!Vacc) {
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false, true><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc)));
+    } else if (filter) {
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc)));
     } else {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32)));
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc)));
     }
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }

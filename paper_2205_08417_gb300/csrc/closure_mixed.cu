@@ -401,42 +401,6 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
     if (warp == 0) tmem_dealloc(tmem, D::tcols);
 }
 
-// Newton logic of the listed cells after a mixed sweep: one warp per list position reads (and
-// clears) its accumulated moment row and runs the shared per-cell step.
-template <int NN>
-__global__ void __launch_bounds__(kThreads)
-mixed_post_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
-                  double *__restrict__ Vacc)
-{
-    constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2;
-    __shared__ double sH[kWarpsM][n * n];
-    __shared__ double sV[kWarpsM][n2];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int32_t *list_in = S.list[k & 1];
-    int32_t *list_out = S.list[(k + 1) & 1];
-    const int cnt_in = S.cnt[k % 3];
-    int32_t *cnt_out = &S.cnt[(k + 1) % 3];
-    for (int it = blockIdx.x * kWarpsM + wib; it < cnt_in; it += gridDim.x * kWarpsM) {
-        const int cell = list_in[it];
-        double *row = Vacc + (size_t)it * n2;
-        if (S.h64[cell]) continue;  // evaluated by the FP64 sweep (its row stays zero)
-        for (int c = lane; c < n2; c += 32) {
-            sV[wib][c] = row[c];
-            row[c] = 0.0;
-        }
-        __syncwarp();
-        const int ph = S.phase[cell];
-        const double lam = ph == PH_NEWTON ? S.lam[cell] : 0.0;
-        const size_t off = (size_t)cell * n;
-        const double ua = lane < n ? u[off + lane] : 0.0;
-        const double al = lane < n ? S.alpha[off + lane] : 0.0;
-        const double di = (ph == PH_NEWTON && lane < n) ? S.dir[off + lane] : 0.0;
-        const double at = lane < n ? (ph == PH_NEWTON ? fma(lam, di, al) : al) : 0.0;
-        newton_post<NN>(T, S, np, cell, ph, lam, at, ua, sV[wib], sH[wib], list_out, cnt_out, lane, true);
-        __syncwarp();
-    }
-}
-
 template <int NN, bool BF16, bool MO>
 int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const double *u, int k,
                       NewtonParams np, const double *alpha_in, double *Vacc, int C, cudaStream_t s,
@@ -459,12 +423,8 @@ int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const
         psi32);
     (void)grid;
     if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
-    if (!MO) {
-        const int need = (C + kWarpsM - 1) / kWarpsM;
-        const int pg = need < mn->nsm * 4 ? (need > 0 ? need : 1) : mn->nsm * 4;
-        mixed_post_kernel<NN><<<pg, kThreads, 0, s>>>(T, S, u, k, np, Vacc);
-        if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
-    }
+    (void)u;
+    (void)np;
     return KITRT_OK;
 }
 

@@ -168,7 +168,7 @@ LaunchScope::~LaunchScope()
 
 static const char *kProfNames[PK_COUNT] = {"closure_begin", "closure_eval_fp64", "closure_finish",
                                            "flux_update", "closure_eval_mixed", "mlp",
-                                           "adjoint", "other"};
+                                           "adjoint", "other", "closure_newton"};
 
 Tables kitrt_mn::tables() const
 {
@@ -510,14 +510,14 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_alloc(mn, &S.list[1], C));
     TRY(dev_alloc(mn, &S.cnt, 16));
     TRY(dev_alloc(mn, &mn->d_psi, C * Qp));
+    TRY(dev_alloc(mn, &mn->d_Vacc, C * (size_t)n2));
+    if (cudaMemset(mn->d_Vacc, 0, sizeof(double) * C * (size_t)n2) != cudaSuccess) {
+        kitrt_mn_destroy(mn);
+        return KITRT_ECUDA;
+    }
     if (p.mode != KITRT_FP64) {
         TRY(dev_alloc(mn, &mn->d_psi32, C * Qp));
-        TRY(dev_alloc(mn, &mn->d_Vacc, C * (size_t)n2));
         if (p.mode == KITRT_LEARNED) TRY(dev_alloc(mn, &mn->d_alpha_nn, C * (size_t)n));
-        if (cudaMemset(mn->d_Vacc, 0, sizeof(double) * C * (size_t)n2) != cudaSuccess) {
-            kitrt_mn_destroy(mn);
-            return KITRT_ECUDA;
-        }
         TRY(dev_alloc(mn, &S.h64, C));
         TRY(dev_alloc(mn, &S.gnorm, C));
     }
@@ -611,15 +611,18 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
     int k = 0;
     for (;;) {
         for (int b = 0; b < batch; ++b, ++k) {
+            // quadrature sweeps write each listed cell's moment row; the thread-per-cell Newton
+            // step then takes every listed cell
             if (mn->p.mode == KITRT_FP64) {
-                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s);
+                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, false, nullptr, mn->d_Vacc);
             } else {
                 // FP64 sweep of the cells handed over in earlier rounds, then the tensor-core sweep
-                // of the others (cells it hands over now wait for the next round, so no cell is
+                // of the others (cells handed over now wait for the next round, so no cell is
                 // evaluated twice in one round)
-                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, true, psi32);
+                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, true, psi32, mn->d_Vacc);
                 if (!rc) rc = launch_eval_mixed(mn, T, mn->st, C, u, k, np, s, psi32);
             }
+            if (!rc) rc = launch_post(mn, T, mn->st, C, u, k, np, mn->d_Vacc, s);
             if (rc) return rc;
         }
         CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -72,7 +72,7 @@ struct NewtonParams {
 
 // Kernel kinds recorded by the tracer.
 enum ProfKind : int { PK_BEGIN = 0, PK_EVAL = 1, PK_FINISH = 2, PK_FLUX = 3, PK_EVAL_MIXED = 4,
-                      PK_MLP = 5, PK_ADJOINT = 6, PK_OTHER = 7, PK_COUNT = 8 };
+                      PK_MLP = 5, PK_ADJOINT = 6, PK_OTHER = 7, PK_POST = 8, PK_COUNT = 9 };
 
 struct ProfRec {
     int kind;
@@ -137,7 +137,9 @@ int launch_learned_pass(kitrt_mn *mn, const Tables &T, const NewtonState &S, int
                         float *psi32, int first, cudaStream_t s);
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s,
-                     bool filter = false, float *psi32 = nullptr);
+                     bool filter = false, float *psi32 = nullptr, double *Vacc = nullptr);
+int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u, int k,
+                NewtonParams np, double *Vacc, cudaStream_t s);
 int launch_finish(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                   double *alpha_out, double *psi, float *psi32, int polish, int compare_prev,
                   cudaStream_t s);

@@ -53,9 +53,16 @@ def test_noalloc_closure_matches_closure_on_two_calls_in_a_row():
         assert torch.equal(st_na, st_ref), call
         ok = (st_ref == 0).cpu().numpy()
         assert ok.mean() > 0.95
-        a1, a2 = a_na.cpu().numpy()[ok], a_ref.cpu().numpy()[ok]
-        err = np.linalg.norm(a1 - a2) / np.linalg.norm(a2)
-        assert err <= 1e-12, (call, err)
+        # both calls converge to the unique minimiser; their answers may differ by rounding
+        # amplified by the conditioning of the dual Hessian (the bound the closure parity tests
+        # use: 1e-9 ||u|| / lambda_min(H) + 1e-12 ||alpha||)
+        a1, a2 = a_na.cpu().numpy(), a_ref.cpu().numpy()
+        un = u.cpu().numpy()
+        for i in np.flatnonzero(ok):
+            e = T.w * np.exp(T.M @ a2[i])
+            lmin = np.linalg.eigvalsh(T.M.T @ (e[:, None] * T.M))[0]
+            bound = 1e-9 * np.linalg.norm(un[i]) / lmin + 1e-12 * np.linalg.norm(a2[i])
+            assert np.linalg.norm(a1[i] - a2[i]) <= bound, (call, i)
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
