@@ -283,7 +283,7 @@ def main():
     build.build()
     W = make_workload(args.workload)
 
-    modes = [args.mode] + [m for m in args.compare.split(",") if m and m != args.mode]
+    modes = [args.mode] + [m for m in args.compare.split(",") if m and m not in (args.mode, "none")]
     peak = fp64_peak_tflops(torch)
     results = {}
     clocks = None
