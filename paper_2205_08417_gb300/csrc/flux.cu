@@ -16,7 +16,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 8;
-constexpr int kBatch = 16;  // cells per warp batch in the FP32 flux
+constexpr int kBatch = 4;  // cells per warp batch in the FP32 flux
 
 template <int NN, typename PsiT>
 __global__ void __launch_bounds__(kWarps * 32)
@@ -109,26 +109,30 @@ flux_update32_kernel(Tables T, const int4 *__restrict__ nbr, const double *__res
             const float nx1 = (float)nrm[6 * (size_t)i + 2], ny1 = (float)nrm[6 * (size_t)i + 3];
             const float nx2 = (float)nrm[6 * (size_t)i + 4], ny2 = (float)nrm[6 * (size_t)i + 5];
             const float *pi_row = psi + (size_t)i * Qp;
+            // upwind rows: the neighbour's row, or the cell's own row as the Neumann ghost (its
+            // fluctuation is then zero) scaled by 0 for the vacuum ghost; loads are issued
+            // unconditionally so that all four rows of a point are in flight together
+            const float *r0 = nb.x >= 0 ? psi + (size_t)nb.x * Qp : pi_row;
+            const float *r1 = nb.y >= 0 ? psi + (size_t)nb.y * Qp : pi_row;
+            const float *r2 = nb.z >= 0 ? psi + (size_t)nb.z * Qp : pi_row;
+            const float g0 = (nb.x >= 0 || bc == 0) ? 1.0f : 0.0f;
+            const float g1 = (nb.y >= 0 || bc == 0) ? 1.0f : 0.0f;
+            const float g2 = (nb.z >= 0 || bc == 0) ? 1.0f : 0.0f;
             float F[n], Fc[n];
 #pragma unroll
             for (int a = 0; a < n; ++a) F[a] = Fc[a] = 0.0f;
+#pragma unroll 2
             for (int q = lane; q < Qp; q += 32) {
-                const float pi = pi_row[q];
+                const float pi = __ldg(pi_row + q);
+                const float p0 = __ldg(r0 + q), p1 = __ldg(r1 + q), p2 = __ldg(r2 + q);
                 const float wx = T.wox32[q], wy = T.woy32[q];
-                const float ghost = bc == 0 ? pi : 0.0f;
+                const float d0 = fmaf(wx, nx0, wy * ny0);
+                const float d1 = fmaf(wx, nx1, wy * ny1);
+                const float d2 = fmaf(wx, nx2, wy * ny2);
                 float s = 0.0f;
-                {
-                    const float d = fmaf(wx, nx0, wy * ny0);
-                    if (d < 0.0f) s = fmaf(d, (nb.x >= 0 ? psi[(size_t)nb.x * Qp + q] : ghost) - pi, s);
-                }
-                {
-                    const float d = fmaf(wx, nx1, wy * ny1);
-                    if (d < 0.0f) s = fmaf(d, (nb.y >= 0 ? psi[(size_t)nb.y * Qp + q] : ghost) - pi, s);
-                }
-                {
-                    const float d = fmaf(wx, nx2, wy * ny2);
-                    if (d < 0.0f) s = fmaf(d, (nb.z >= 0 ? psi[(size_t)nb.z * Qp + q] : ghost) - pi, s);
-                }
+                s = fmaf(fminf(d0, 0.0f), fmaf(g0, p0, -pi), s);
+                s = fmaf(fminf(d1, 0.0f), fmaf(g1, p1, -pi), s);
+                s = fmaf(fminf(d2, 0.0f), fmaf(g2, p2, -pi), s);
 #pragma unroll
                 for (int a = 0; a < n; ++a) {
                     const float y = fmaf(T.Mt32[a * Qp + q], s, -Fc[a]);
@@ -179,8 +183,19 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
     int need = (C + kWarps - 1) / kWarps;
     int cap = mn->nsm * 8;
     int grid = need < cap ? (need > 0 ? need : 1) : cap;
+    // persistent grid of as many blocks as fit at once, batches of kBatch cells dealt round-robin
+    // to warps (no partial second wave)
+    int resident = 0;
+    switch (mn->N) {
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<1>, kWarps * 32, 0); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<2>, kWarps * 32, 0); break;
+    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<3>, kWarps * 32, 0); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<4>, kWarps * 32, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<5>, kWarps * 32, 0); break;
+    }
+    if (resident < 1) resident = 1;
     const int need32 = (C + kWarps * kBatch - 1) / (kWarps * kBatch);
-    const int grid32 = need32 < cap ? (need32 > 0 ? need32 : 1) : cap;
+    const int grid32 = need32 < mn->nsm * resident ? (need32 > 0 ? need32 : 1) : mn->nsm * resident;
     LaunchScope ls(mn, PK_FLUX, s, C);
 #define FLUX_CASE(NN)                                                                          \
     case NN:                                                                                   \
