@@ -139,14 +139,21 @@ int32_t kitrt_mn_destroy(kitrt_mn *mn);
 /* Sizes: moments n, quadrature points Q of the full rule and Q' after folding. */
 int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_t *nquad_folded);
 
-/* Work accounting of one cell evaluation of the dual (one quadrature pass): moments n, degree-2N
- * moments n2, folded points Q', non-zero Gaunt coefficients, and the algorithmic FP64 flops of
- * the pass without exp: 2nQ' (exponents) + Q' (weights) + 2 n2 Q' (moment sums) + 2 nnz
- * (Hessian) + n^3/3 + 2n^2 (Cholesky and solves). */
+/* Work accounting of one cell evaluation of the dual (one quadrature pass) in the solver's mode:
+ * moments n, degree-2N moments n2, folded points Q', non-zero Gaunt coefficients, and
+ *   sweep_fp64_flops   FP64 flops of the quadrature sweep without exp: 2nQ' (exponents) + Q'
+ *                      (weights) + 2 n2 Q' (FP64 mode: all moments) or 2 n Q' (mixed modes:
+ *                      gradient moments only);
+ *   exps               exponentials per evaluation (Q');
+ *   tensor_flops       mixed modes: 3 x 2 (n2 - n) Q' on tensor cores (three split products);
+ *   newton_flops       the per-cell Newton step: 2 nnz (Hessian) + n^3/3 + 2n^2 (Cholesky,
+ *                      solves). */
 typedef struct {
     int32_t nmom, nmom2, nquad_folded, gaunt_nnz;
-    double flops_per_eval;
-    double exps_per_eval;
+    double sweep_fp64_flops;
+    double exps;
+    double tensor_flops;
+    double newton_flops;
 } kitrt_work;
 int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out);
 

@@ -543,12 +543,15 @@ int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out)
 {
     if (!mn || !out) return KITRT_EINVAL;
     const double n = mn->n, n2 = mn->n2, Qf = mn->Qf;
+    const bool fp64 = mn->p.mode == KITRT_FP64;
     out->nmom = mn->n;
     out->nmom2 = mn->n2;
     out->nquad_folded = mn->Qf;
     out->gaunt_nnz = mn->gaunt_nnz;
-    out->flops_per_eval = 2 * n * Qf + Qf + 2 * n2 * Qf + 2.0 * mn->gaunt_nnz + n * n * n / 3 + 2 * n * n;
-    out->exps_per_eval = Qf;
+    out->sweep_fp64_flops = 2 * n * Qf + Qf + 2 * (fp64 ? n2 : n) * Qf;
+    out->exps = Qf;
+    out->tensor_flops = fp64 ? 0.0 : 3.0 * 2.0 * (n2 - n) * Qf;
+    out->newton_flops = 2.0 * mn->gaunt_nnz + n * n * n / 3 + 2 * n * n;
     return KITRT_OK;
 }
 

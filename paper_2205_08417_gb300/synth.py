@@ -144,5 +144,5 @@ WORKLOADS = {
     "m2_line_source_4k": dict(k=45, lo=-1.5, hi=1.5, seed=1, N=2, order=10),
     "m3_line_source_100k": dict(k=224, lo=-1.5, hi=1.5, seed=2, N=3, order=20),
     "m3_blocks_60k": dict(k=173, lo=0.0, hi=7.0, seed=3, N=3, order=10),
-    "m5_line_source_1m": dict(k=707, lo=-1.5, hi=1.5, seed=5, N=5, order=30),
+    "m5_line_source_1m": dict(k=707, lo=-1.5, hi=1.5, seed=5, N=5, order=30, blocks=True),
 }

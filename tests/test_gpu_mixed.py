@@ -177,3 +177,43 @@ def test_mixed_d2_size_sampled_against_oracle(K, mode):
     O.mn_run(T, Gs, us, als, sa[cells], ss[cells], q[cells], dt, 1)
     pos = np.searchsorted(cells, sample)
     assert rel_l2(u_gpu[sample, 0], us[pos, 0]) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed_tf32"])
+def test_m5_million_triangles_sampled_against_oracle(K, mode):
+    """The large configuration: ~1M triangles (707^2 points), M_5 (21 moments), order-30
+    quadrature (1800 points, 900 folded), line-source start in a seeded 7x7 block medium
+    (sigma_a in [0,10], sigma_s in [0,1]). Two steps on the GPU, then a third checked on sampled
+    cells against the oracle (each recomputed on a submesh of it and its neighbours)."""
+    import bench
+    W = bench.make_workload("m5_line_source_1m")
+    m = W["mesh"]
+    mesh = K.Mesh(m.xy, m.tri)
+    C = W["C"]
+    assert C > 990_000
+    dt = 0.4 * mesh.geometry()["min_inradius"]
+    s = K.MNSolver(mesh, 5, 30, mode=mode, tau=1e-10 if mode == "fp64" else 1e-8)
+    ud = dev(W["u0"])
+    ad = s.isotropic_alpha(ud)
+    sa, ss, q = dev(W["sa"]), dev(W["ss"]), dev(W["q"])
+    s.step(ud, ad, sa, ss, q, dt=dt, nsteps=2)
+    u_start, a_start = ud.cpu().numpy().copy(), ad.cpu().numpy().copy()
+    s.step(ud, ad, sa, ss, q, dt=dt, nsteps=1)
+    u_gpu = ud.cpu().numpy()
+    G_nbr = mesh.geometry()["nbr"]
+    rng = np.random.default_rng(5)
+    r2 = (W["cen"] ** 2).sum(axis=1)
+    front = np.flatnonzero(r2 < 0.01)
+    sample = np.unique(np.concatenate([rng.choice(C, 60, replace=False),
+                                       rng.choice(front, min(60, front.size), replace=False)]))
+    cells = np.unique(np.concatenate([sample, G_nbr[sample][G_nbr[sample] >= 0]]))
+    T = O.Tables(5, 30)
+    Gs = O.Geometry(m.xy, m.tri[cells])
+    us, als = u_start[cells].copy(), a_start[cells].copy()
+    nf, _ = O.mn_run(T, Gs, us, als, W["sa"][cells], W["ss"][cells], W["q"][cells], dt, 1)
+    assert nf == 0
+    pos = np.searchsorted(cells, sample)
+    if mode == "fp64":
+        assert rel_l2(u_gpu[sample], us[pos]) <= 1e-11
+    else:
+        assert rel_l2(u_gpu[sample, 0], us[pos, 0]) <= 1e-5
