@@ -35,6 +35,22 @@ UNIT = "cell-updates/s"
 WORKLOAD = "m3_line_source_100k"
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over all ranks (the job takes as long as its
+    slowest replica)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def replica_throughput(cells, steps, max_ms, world):
+    """Whole-job cell-updates/s of `world` independent replicas, each advancing `cells` cells by
+    `steps` steps, timed by the slowest replica."""
+    return world * cells * steps / (max_ms / 1e3)
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,16 +324,13 @@ def main():
             clocks = cs.stop()
         results[mode] = r
     head = results[args.mode]
-    ms = head["ms"]
     if world > 1:
-        t = torch.tensor([ms, head["e2e_ms"]], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+        ms, e2e_ms = max_over_ranks([head["ms"], head.get("e2e_ms", float("nan"))], "cuda")
     else:
-        e2e_ms = head.get("e2e_ms", float("nan"))
+        ms, e2e_ms = head["ms"], head.get("e2e_ms", float("nan"))
     C = W["C"]
-    value = world * C * args.steps / (ms / 1e3)
-    e2e_value = world * C * args.steps / (e2e_ms / 1e3)
+    value = replica_throughput(C, args.steps, ms, world)
+    e2e_value = replica_throughput(C, args.steps, e2e_ms, world)
 
     n, Qf = W["n"], W["order"] ** 2  # folded points Q' = Q/2 = order^2
     work = head["solver"].work()
