@@ -67,6 +67,10 @@ def _declare(L):
                                  _dp, _bp, d, i, i, d, i, i, _dp, _dp, _dp, _dp, _dp]
     L.orc_mn_objective.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _ip, _dp, _dp,
                                    _dp, _bp, d, i, i, d, i, i, _dp, _dp, _dp]
+    L.orc_sn_step.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
+                              d, i, _dp, _dp, i]
+    L.orc_sn_run.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
+                             d, i, i, _dp, _dp, i]
     L.orc_mlp_forward.argtypes = [i, i, i, i, _dp, _dp, _dp]
     L.orc_mlp_loss_grad.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp]
     L.orc_mlp_loss_grad.restype = d
@@ -182,6 +186,40 @@ def flux_update(T: Tables, G: Geometry, psi, u, sigma_a, sigma_s, qsrc, dt, bc=0
                           _d(np.ascontiguousarray(sigma_s, dtype=np.float64)),
                           _d(np.ascontiguousarray(qsrc, dtype=np.float64)), dt, bc, _d(u),
                           nthreads)
+
+
+def _scatter_coefficients(T: Tables, g):
+    """g_l for l = 0..N (None: isotropic scattering, g = (1, 0, ..., 0))."""
+    if g is None:
+        g = np.zeros(T.N + 1)
+        g[0] = 1.0
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    assert g.shape == (T.N + 1,)
+    return g
+
+
+def sn_step(T: Tables, G: Geometry, psi, sigma_a, sigma_s, qsrc, dt, g=None, bc=0, nthreads=0):
+    """One S_N step of the ordinates psi [C, Q] (full quadrature); returns the new ordinates.
+    Scattering O Sigma M truncated at the degree N of T, Sigma = sigma_s diag(g_l)."""
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    out = np.zeros_like(psi)
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    lib().orc_sn_step(G.C, T.n, T.N, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                      _d(G.nrm), _d(G.area), f(sigma_a), f(sigma_s), f(qsrc),
+                      _d(_scatter_coefficients(T, g)), dt, bc, _d(psi), _d(out), nthreads)
+    return out
+
+
+def sn_run(T: Tables, G: Geometry, psi, sigma_a, sigma_s, qsrc, dt, nsteps, g=None, bc=0,
+           nthreads=0):
+    """nsteps S_N steps in place on psi [C, Q]."""
+    assert psi.dtype == np.float64 and psi.flags.c_contiguous
+    tmp = np.zeros_like(psi)
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    lib().orc_sn_run(G.C, T.n, T.N, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                     _d(G.nrm), _d(G.area), f(sigma_a), f(sigma_s), f(qsrc),
+                     _d(_scatter_coefficients(T, g)), dt, bc, nsteps, _d(psi), _d(tmp), nthreads)
+    return psi
 
 
 def mn_run(T: Tables, G: Geometry, u, alpha, sigma_a, sigma_s, qsrc, dt, nsteps, bc=0, tau=1e-10,

@@ -19,6 +19,8 @@
  *     first-order update [Sec. 4.2, explicit iteration] with isotropic scattering, absorption and
  *     an isotropic source [Sec. 3.1 moment equations: scattering diagonal in moments].
  *   - Discrete adjoint of that step (exact transpose, closure derivative dalpha/du = H^-1).
+ *   - The S_N step of the nodal system [Sec. 2, Eq. SNEqns2] with the P_N form O Sigma M of the
+ *     scattering operator and the same upwind flux applied per ordinate.
  *   - Plain MLP (softplus) forward/backward and Adam, for the learned-closure gradient checks.
  *
  * Quadrature sums here always run over the full, unfolded point set Q; the CUDA path folds the
@@ -495,6 +497,91 @@ void orc_flux_update(int C, int n, int Q, const double *M, const double *w, cons
         }
     }
     (void)nthreads;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* S_N step [Sec. 2, Eq. SNEqns2; Sec. 4.2 explicit iteration; Sec. 4.4 upwind flux per         */
+/* ordinate]                                                                                  */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Degree l of each basis function, in the order of orc_basis. */
+static void orc_basis_degrees(int N, int *deg)
+{
+    int idx = 0;
+    for (int l = 0; l <= N; ++l)
+        for (int k = -l; k <= l; ++k) {
+            int ak = k < 0 ? -k : k;
+            if (((l + ak) & 1) != 0) continue;
+            deg[idx++] = l;
+        }
+}
+
+/* One explicit S_N step of the nodal system (the ordinates psi_q of the full quadrature):
+ *   psi'_iq = psi_iq - dt/A_i sum_f (Omega_q . n_if) [upwind psi]
+ *             - dt (sigma_a,i + sigma_s,i) psi_iq + dt (O Sigma_i M psi_i)_q + dt q_i,
+ * with the scattering in its P_N form O Sigma M of Eq. SNEqns2: M = (w_q m(Omega_q)) maps the
+ * ordinates to the n moments of degree <= N, Sigma_i = sigma_s,i diag(g_l(a)) scales moment a by
+ * the kernel's coefficient of its degree l(a) (g_0 = 1: sigma_s is the total scattering
+ * cross-section; isotropic scattering is g = (1, 0, ..., 0)), and O = (m(Omega_q)) maps back.
+ * The upwind value on face f is psi_iq when Omega_q . n_if > 0, else the neighbour's psi_jq,
+ * or at the boundary the cell's own value (bc 0) or 0 (bc 1, vacuum). psi and psi_out are
+ * [C x Q], distinct arrays. */
+void orc_sn_step(int C, int n, int N, int Q, const double *M, const double *w, const double *ox,
+                 const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+                 const double *sigma_a, const double *sigma_s, const double *qsrc,
+                 const double *g, double dt, int bc, const double *psi, double *psi_out,
+                 int nthreads)
+{
+    int deg[64];
+    orc_basis_degrees(N, deg);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(static)
+#endif
+    for (int i = 0; i < C; ++i) {
+        const double *pi = psi + (size_t)i * Q;
+        /* moments of the cell's ordinates, then the scattered moments */
+        double s[64];
+        for (int a = 0; a < n; ++a) {
+            double v = 0.0;
+            for (int q = 0; q < Q; ++q) v += w[q] * M[(size_t)q * n + a] * pi[q];
+            s[a] = sigma_s[i] * g[deg[a]] * v;
+        }
+        for (int q = 0; q < Q; ++q) {
+            double tr = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                int j = nbr[3 * i + k];
+                double dot = ox[q] * nrm[6 * i + 2 * k] + oy[q] * nrm[6 * i + 2 * k + 1];
+                double up;
+                if (dot > 0.0)
+                    up = pi[q];
+                else if (j >= 0)
+                    up = psi[(size_t)j * Q + q];
+                else
+                    up = bc == 0 ? pi[q] : 0.0;
+                tr += dot * up;
+            }
+            double sc = 0.0;
+            for (int a = 0; a < n; ++a) sc += M[(size_t)q * n + a] * s[a];
+            psi_out[(size_t)i * Q + q] = pi[q] - dt / area[i] * tr -
+                                         dt * (sigma_a[i] + sigma_s[i]) * pi[q] + dt * sc +
+                                         dt * qsrc[i];
+        }
+    }
+    (void)nthreads;
+}
+
+/* nsteps S_N steps; psi [C x Q] is advanced in place (tmp is scratch of the same size). */
+void orc_sn_run(int C, int n, int N, int Q, const double *M, const double *w, const double *ox,
+                const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+                const double *sigma_a, const double *sigma_s, const double *qsrc, const double *g,
+                double dt, int bc, int nsteps, double *psi, double *tmp, int nthreads)
+{
+    for (int s = 0; s < nsteps; ++s) {
+        orc_sn_step(C, n, N, Q, M, w, ox, oy, nbr, nrm, area, sigma_a, sigma_s, qsrc, g, dt, bc,
+                    psi, tmp, nthreads);
+        memcpy(psi, tmp, sizeof(double) * (size_t)C * Q);
+    }
 }
 
 /* nsteps explicit M_N steps. Each step: closure of every cell (warm start alpha), ansatz psi,
