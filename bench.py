@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--t-start", type=float, default=0.25,
                     help="simulated time reached by untimed set-up steps before warm-up")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sn", action="store_true", help="skip the S_N step measurement")
     ap.add_argument("--tau", type=float, default=1e-10, help="Newton tolerance of the FP64 mode")
     ap.add_argument("--tau-mixed", type=float, default=1e-8,
                     help="Newton tolerance of the mixed modes (matched to their FP32 ansatz)")
@@ -217,6 +218,11 @@ def train_network(K, torch, W, samples, seed=4):
     return net
 
 
+def log(msg):
+    """Progress to stderr (stdout carries the one JSON line)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None):
     mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
     s = K.MNSolver(mesh, W["N"], W["order"], mode=mode, tau=tau)
@@ -230,10 +236,12 @@ def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None)
     dt = 0.4 * geo["min_inradius"]
     setup = int(round(t_start / dt))
     before = 0
+    t0 = time.perf_counter()
     if setup:
         before += s.step(u, alpha, sa, ss, q, dt=dt, nsteps=setup, stats=True)[1]["launches"]
     before += s.step(u, alpha, sa, ss, q, dt=dt, nsteps=warmup, stats=True)[1]["launches"]
     torch.cuda.synchronize()
+    log(f"mode {mode}: {setup} set-up + {warmup} warm-up steps in {time.perf_counter() - t0:.1f} s")
     s.profile(True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -263,6 +271,60 @@ def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None)
         out["e2e_ms"] = e0.elapsed_time(e1)
         out["e2e_bytes"] = C * n * 8
     return out
+
+
+def run_sn(K, torch, W, steps, warmup, fp32, hbm_peak):
+    """S_N steps (the nodal system with isotropic scattering) on the same mesh, quadrature and
+    line-source start: ordinates psi = Phi / (4 pi) at the folded points, [C x Q'] resident on the
+    device, double-buffered. Roofline: algorithmic bytes per cell = own row read + written
+    (2 Q' b) + cell data (neighbours 16 B, normals 48 B, area 8 B, sigma_a, sigma_s, q 24 B); the
+    three upwind rows are other cells' rows and count once."""
+    mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
+    s = K.MNSolver(mesh, W["N"], W["order"])
+    C, Qf = W["C"], s.Qf
+    phi = W["u0"][:, 0] * math.sqrt(4 * math.pi)
+    dtype = torch.float32 if fp32 else torch.float64
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    psi = d(np.repeat((phi / (4 * math.pi))[:, None], Qf, axis=1)).to(dtype)
+    work = torch.empty_like(psi)
+    sa, ss, q = d(W["sa"]), d(W["ss"]), d(W["q"])
+    dt = 0.4 * mesh.geometry()["min_inradius"]
+    s.sn_step(psi, work, sa, ss, q, dt=dt, nsteps=max(warmup, 3))
+    torch.cuda.synchronize()
+    s.profile(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.sn_step(psi, work, sa, ss, q, dt=dt, nsteps=steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    pe = s.profile_read()["sn_step"]
+    s.profile(False)
+    b = 4 if fp32 else 8
+    per_cell = 2 * Qf * b + 96
+    launch_ms = pe["total_ms"] / pe["launches"]
+    gbs = C * per_cell / (launch_ms / 1e3) / 1e9
+    out = {"cell_updates_per_s": C * steps / (ms / 1e3), "ms_per_step": ms / steps,
+           "dtype": "f32" if fp32 else "f64", "scattering": "isotropic",
+           "roofline": {"kernel": "sn_step", "bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                        "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+                        "bytes_per_cell": per_cell, "avg_launch_ms": launch_ms,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+    if not fp32:
+        # per ordinate: 3 face dots (2 flops each), 3 fluctuation terms (3 each), moment (2) and
+        # scattering (2) and update (4 FP64 flops)
+        flops = C * Qf * (6 + 9 + 2 + 2 + 4)
+        out["fp64_tflops"] = flops / (launch_ms / 1e3) / 1e12
+    return out
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # fallback figure of an earlier GB300 measurement
 
 
 def main():
@@ -310,19 +372,32 @@ def main():
     peak = fp64_peak_tflops(torch)
     results = {}
     clocks = None
+    log(f"workload {args.workload}: {W['C']} cells, modes {modes}")
     net = train_network(K, torch, W, args.train_samples) if "learned" in modes else None
+    if net is not None:
+        log(f"learned closure trained: {net.info}")
     for mode in modes:
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         cs = ClockSampler(local) if mode == args.mode else None
         tau = args.tau if mode == "fp64" else args.tau_mixed
-        r = run_mode(K, torch, W, mode, args.steps, args.warmup, args.t_start, tau, e2e=not args.no_e2e,
-                     net=net if mode == "learned" else None)
+        try:
+            r = run_mode(K, torch, W, mode, args.steps, args.warmup, args.t_start, tau,
+                         e2e=not args.no_e2e, net=net if mode == "learned" else None)
+        except K.KitrtError as exc:
+            print(f"bench: mode {mode} (tau {tau}) failed: {exc}", file=sys.stderr, flush=True)
+            raise
         r["tau"] = tau
+        log(f"mode {mode}: {r['ms'] / args.steps:.3f} ms/step, stats {r['stats']}")
         if cs is not None:
             clocks = cs.stop()
         results[mode] = r
+    sn = None
+    if not args.no_sn:
+        hp = hbm_peak_gbs()
+        sn = {"sn_fp32": run_sn(K, torch, W, args.steps, args.warmup, True, hp),
+              "sn_fp64": run_sn(K, torch, W, args.steps, args.warmup, False, hp)}
     head = results[args.mode]
     if world > 1:
         ms, e2e_ms = max_over_ranks([head["ms"], head.get("e2e_ms", float("nan"))], "cuda")
@@ -369,8 +444,10 @@ def main():
                    "quad_points": 2 * W["order"] ** 2, "quad_points_folded": Qf,
                    "mode": args.mode, "dt": head["dt"], "tau": head["tau"], "parallelism": f"replicas{world}",
                    "t_start": args.t_start, "setup_steps": head["setup"],
-                   "l2": "working set > L2: FP64 psi (C x Q' x 8 B = "
-                         f"{C * (Qf + 31) // 32 * 32 * 8 / 1e6:.0f} MB) written and re-read every step"},
+                   "l2": f"working set > L2: {'FP64' if args.mode == 'fp64' else 'FP32'} psi (C x Q'pad x "
+                         f"{8 if args.mode == 'fp64' else 4} B = "
+                         f"{C * ((Qf + 31) // 32 * 32) * (8 if args.mode == 'fp64' else 4) / 1e6:.0f} MB) "
+                         "written and re-read every step; no flush"},
         "closures_per_s": closures_per_s,
         "evaluations_per_cell_step": head["stats"]["evaluations"] / (C * args.steps),
         "roofline": {"kernel": ekey,
@@ -394,6 +471,7 @@ def main():
                       "evaluations_per_cell_step": r["stats"]["evaluations"] / (C * args.steps)}
                   for m, r in results.items()},
         "error": errors,
+        "sn": sn,
         "e2e": None if args.no_e2e else {
             "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": head["e2e_bytes"],
             "d2h_bytes_per_step": head["e2e_bytes"]},

@@ -229,6 +229,31 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
 int32_t kitrt_closure_noalloc(const kitrt_mn *mn, const double *u, double *alpha,
                               int32_t *status, int32_t ncells, void *stream);
 
+/* S_N steps of the nodal (discrete-ordinates) system [Sec. 2, Eq. SNEqns2]: explicit first-order
+ * finite volumes [Sec. 4.2] with the upwind flux of Sec. 4.4 applied to every ordinate,
+ *   psi'_iq = psi_iq - dt/A_i sum_f (Omega_q . n_if) psi_up - dt (sigma_a,i + sigma_s,i) psi_iq
+ *             + dt (O Sigma_i M psi_i)_q + dt q_i,
+ * on the solver's folded quadrature (kitrt_mn_quadrature; the +-mu ordinates of the 2D problem
+ * are equal). The scattering is the P_N form of Eq. SNEqns2 truncated at the solver's degree N:
+ * moment a of the ordinates, sum_q w_q m_a(Omega_q) psi_q, is scaled by sigma_s g_l(a) (l(a) the
+ * degree of basis function a) and mapped back through m(Omega_q). Boundary faces take the
+ * solver's boundary condition (Neumann: the cell's own ordinate; vacuum: 0). No closure is
+ * involved; the solver handle supplies the mesh, the quadrature and the basis.
+ *   psi      device [C x Q'] ordinates (Q' = nquad_folded of kitrt_mn_sizes, row-major, no
+ *            padding), FP64, or FP32 when fp32 != 0; advanced in place by nsteps steps.
+ *   work     device scratch of the same size and type, not overlapping psi.
+ *   sigma_a, sigma_s, q  device [C] FP64 per-cell absorption, total scattering, isotropic source.
+ *   g        host [N+1] Legendre coefficients of the scattering kernel relative to its total
+ *            (g[0] must be 1; g_l = c^l is Henyey-Greenstein with asymmetry c), or NULL for
+ *            isotropic scattering.
+ *   dt       time step; dt <= 0 selects cfl * (smallest inradius).
+ * Asynchronous on `stream` (nsteps launches, plus one device copy when nsteps is odd).
+ * KITRT_EINVAL for NULL arguments, nsteps < 0, overlapping buffers, g[0] != 1 or a non-finite
+ * g. */
+int32_t kitrt_sn_step(kitrt_mn *mn, void *psi, void *work, int32_t fp32, const double *sigma_a,
+                      const double *sigma_s, const double *q, const double *g, double dt,
+                      int32_t nsteps, void *stream);
+
 /* Discrete adjoint of nsteps FP64 steps (solver in KITRT_FP64 mode): the objective
  *   J = sum_{s=0}^{nsteps-1} dt sum_{i in target} A_i sigma_a,i u^s_i0 / m_0
  * (absorbed energy in the target cells; u_0/m_0 is the scalar flux <psi>) and its gradient with

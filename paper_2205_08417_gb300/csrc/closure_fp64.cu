@@ -136,7 +136,7 @@ predict_kernel(NewtonState S, const double *__restrict__ u, NewtonParams np)
 // the next Newton direction.
 // ---------------------------------------------------------------------------------------------
 // FUSED: the warp also runs the per-cell Newton logic (used by the allocation-free closure);
-// otherwise the sweep writes the cell's moment row to Vacc[list slot] for post_thread_kernel.
+// otherwise the sweep writes the cell's moment row to Vacc[list slot] for the post kernel.
 template <int NN, bool FILTER, bool FUSED>
 __global__ void __launch_bounds__(kWarps * 32)
 eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,

@@ -168,7 +168,7 @@ LaunchScope::~LaunchScope()
 
 static const char *kProfNames[PK_COUNT] = {"closure_begin", "closure_eval_fp64", "closure_finish",
                                            "flux_update", "closure_eval_mixed", "mlp",
-                                           "adjoint", "other", "closure_newton"};
+                                           "adjoint", "other", "closure_newton", "sn_step"};
 
 Tables kitrt_mn::tables() const
 {
@@ -351,6 +351,7 @@ int32_t kitrt_mn_destroy(kitrt_mn *mn)
     }
     for (void *p : mn->allocs) cudaFree(p);
     if (mn->h_cnt) cudaFreeHost(mn->h_cnt);
+    if (mn->h_sn_flag) cudaFreeHost(mn->h_sn_flag);
     delete mn;
     return KITRT_OK;
 }
@@ -483,6 +484,17 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_upload(mn, &mn->d_w32, w32));
     TRY(dev_upload(mn, &mn->d_wox32, wox32));
     TRY(dev_upload(mn, &mn->d_woy32, woy32));
+    // unweighted folded directions for the S_N step (0 on padding)
+    std::vector<double> oxp(Qp, 0.0), oyp(Qp, 0.0);
+    for (int q = 0; q < Qf; ++q) {
+        oxp[q] = mn->h_ox[q];
+        oyp[q] = mn->h_oy[q];
+    }
+    std::vector<float> oxp32(oxp.begin(), oxp.end()), oyp32(oyp.begin(), oyp.end());
+    TRY(dev_upload(mn, &mn->d_ox, oxp));
+    TRY(dev_upload(mn, &mn->d_oy, oyp));
+    TRY(dev_upload(mn, &mn->d_ox32, oxp32));
+    TRY(dev_upload(mn, &mn->d_oy32, oyp32));
     // 2^(j/256), j = 0..255, rounded to double from extended precision
     std::vector<double> exptab(256);
     for (int j = 0; j < 256; ++j) exptab[j] = (double)exp2l((long double)j / 256.0L);
@@ -522,6 +534,16 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
         TRY(dev_alloc(mn, &S.gnorm, C));
     }
     if (cudaMallocHost(&mn->h_cnt, 16 * sizeof(int32_t)) != cudaSuccess) {
+        kitrt_mn_destroy(mn);
+        return KITRT_ENOMEM;
+    }
+    TRY(dev_alloc(mn, &mn->d_sn_flag, 1));
+    {
+        double *cellc = nullptr;
+        TRY(dev_alloc(mn, &cellc, C * 12));
+        mn->d_sn_cell = cellc;
+    }
+    if (cudaMallocHost(&mn->h_sn_flag, sizeof(int32_t)) != cudaSuccess) {
         kitrt_mn_destroy(mn);
         return KITRT_ENOMEM;
     }

@@ -72,7 +72,8 @@ struct NewtonParams {
 
 // Kernel kinds recorded by the tracer.
 enum ProfKind : int { PK_BEGIN = 0, PK_EVAL = 1, PK_FINISH = 2, PK_FLUX = 3, PK_EVAL_MIXED = 4,
-                      PK_MLP = 5, PK_ADJOINT = 6, PK_OTHER = 7, PK_POST = 8, PK_COUNT = 9 };
+                      PK_MLP = 5, PK_ADJOINT = 6, PK_OTHER = 7, PK_POST = 8, PK_SN = 9,
+                      PK_COUNT = 10 };
 
 struct ProfRec {
     int kind;
@@ -94,6 +95,8 @@ struct kitrt_mn {
     float *d_Mhi32 = nullptr;            // [NP x Qp] TF32-rounded degree-(N+1..2N) basis (mixed)
     unsigned short *d_Mhi16 = nullptr;   // [NP x Qp] BF16 copy
     float *d_wox32 = nullptr, *d_woy32 = nullptr;
+    double *d_ox = nullptr, *d_oy = nullptr;  // [Qp] folded directions (0 on padding), S_N step
+    float *d_ox32 = nullptr, *d_oy32 = nullptr;
     double *d_V = nullptr;               // [C x n2] moments scratch (kitrt_hessian)
     double *d_Vacc = nullptr;            // [C x n2] mixed sweeps: moment accumulators per list slot
     double *d_exptab = nullptr;          // [256] 2^(j/256)
@@ -106,6 +109,9 @@ struct kitrt_mn {
     double *d_psi = nullptr;   // [C x Qp] FP64 ansatz
     float *d_psi32 = nullptr;  // [C x Qp] FP32 ansatz (mixed modes)
     int32_t *h_cnt = nullptr;  // pinned copy of st.cnt
+    int32_t *d_sn_flag = nullptr;  // S_N step: device status (KITRT_ETIMEOUT on an expired wait)
+    int32_t *h_sn_flag = nullptr;  // pinned copy
+    void *d_sn_cell = nullptr;     // [C x 12] per-cell coefficients of the S_N step (FP32 or FP64)
     std::vector<void *> allocs;
     // tracing
     bool prof_on = false;

@@ -129,7 +129,15 @@ __device__ void newton_post(const Tables &T, const NewtonState &S, const NewtonP
     }
     if (!accept) {
         const int h = S.halv[cell] + 1;
-        if (h > np.max_halvings) {
+        if (h > np.max_halvings && mixed && !S.h64[cell]) {
+            // as in newton_post_thread: restart from the accepted point with the FP64 Hessian
+            if (lane == 0) {
+                S.h64[cell] = 1;
+                S.halv[cell] = 0;
+                S.phase[cell] = PH_INIT;
+            }
+            push(list_out, cnt_out, cell, lane);
+        } else if (h > np.max_halvings) {
             fail(S, cell, KITRT_ELINESEARCH, lane);
         } else {
             if (lane == 0) {
@@ -220,155 +228,16 @@ __device__ __forceinline__ void push_agg(int32_t *list, int32_t *cnt, int cell, 
     if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = cell;
 }
 
-// One-thread version of newton_post for the scalar Newton logic after an evaluation: V is the
-// cell's row of n2 degree-2N moments (global memory). Every FP64 instruction of this logic keeps
-// all 32 lanes busy (32 cells per warp), which matters on a GPU whose FP64 pipe is narrow.
-// Returns true when the cell continues (must be appended to the next list).
-template <int NN>
-__device__ bool newton_post_thread(const Tables &T, const NewtonState &S, const NewtonParams &np,
-                                   int cell, const double *__restrict__ V,
-                                   const double *__restrict__ u, bool mixed, int &evals_out)
-{
-    constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2, npairs = Dims<NN>::npairs;
-    const size_t off = (size_t)cell * n;
-    const int ph = S.phase[cell];
-    const double lam = ph == PH_NEWTON ? S.lam[cell] : 0.0;
-    double at[n], ua[n];
-    double au = 0.0;
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-        const double al = S.alpha[off + a];
-        at[a] = ph == PH_NEWTON ? fma(lam, S.dir[off + a], al) : al;
-        ua[a] = u[off + a];
-        au = fma(at[a], ua[a], au);
-    }
-    bool finite = true;
-#pragma unroll
-    for (int c = 0; c < n2; ++c) finite = finite && isfinite(V[c]);
-    const double fs = V[0] / T.m0;
-    const double ft = fs - au;
-    const int ev = S.evals[cell] + 1;
-    S.evals[cell] = ev;
-    evals_out = ev;
-    auto fail_t = [&](int code) {
-        S.status[cell] = code;
-        S.phase[cell] = PH_DONE;
-        atomicAdd(&S.cnt[3], 1);
-    };
-    bool accept;
-    if (ph == PH_INIT) {
-        if (!finite) {
-            fail_t(KITRT_ENOTREALIZABLE);
-            return false;
-        }
-        accept = true;
-    } else {
-        const double fs0 = S.fsum[cell], f0 = S.f0[cell];
-        const double slack = 64.0 * 2.220446049250313e-16 * (fs0 + fabs(fs0 - f0));
-        accept = finite && ft <= f0 + np.c1 * lam * S.gd[cell] + slack;
-    }
-    if (!accept) {
-        const int h = S.halv[cell] + 1;
-        if (h > np.max_halvings) {
-            fail_t(KITRT_ELINESEARCH);
-            return false;
-        }
-        S.halv[cell] = h;
-        S.lam[cell] = 0.5 * lam;
-        return true;
-    }
-    // Hessian (packed lower) from the Gaunt coefficients, then Cholesky with 1/L_jj on the diagonal
-    double Lp[npairs];
-#pragma unroll
-    for (int p = 0; p < npairs; ++p) {
-        double h = 0.0;
-        for (int t = T.gstart[p]; t < T.gstart[p + 1]; ++t) h = fma(T.gcoef[t], V[T.gidx[t]], h);
-        Lp[p] = h;
-    }
-    bool spd = true;
-#pragma unroll
-    for (int j = 0; j < n; ++j) {
-        double d = Lp[tri_idx(j, j)];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d = fma(-Lp[tri_idx(j, k)], Lp[tri_idx(j, k)], d);
-        spd = spd && d > 0.0;
-        const double rinv = rsqrt(d > 0.0 ? d : 1.0);
-        Lp[tri_idx(j, j)] = rinv;
-#pragma unroll
-        for (int i = j + 1; i < n; ++i) {
-            double s = Lp[tri_idx(i, j)];
-#pragma unroll
-            for (int k = 0; k < j; ++k) s = fma(-Lp[tri_idx(i, k)], Lp[tri_idx(j, k)], s);
-            Lp[tri_idx(i, j)] = s * rinv;
-        }
-    }
-    if (!spd) {
-        if (mixed) {
-            S.h64[cell] = 1;  // tensor-core rounding broke positive definiteness: redo in FP64
-            return true;
-        }
-        fail_t(KITRT_ECHOL);
-        return false;
-    }
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-        S.alpha[off + a] = at[a];
-        S.U[off + a] = V[a];
-    }
-    S.fsum[cell] = fs;
-    S.f0[cell] = ft;
-#pragma unroll
-    for (int p = 0; p < npairs; ++p) S.L[(size_t)cell * npairs + p] = Lp[p];
-    // d = -H^-1 g
-    double y[n];
-    double gn2 = 0.0, un2 = 0.0;
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-        const double g = V[a] - ua[a];
-        gn2 = fma(g, g, gn2);
-        un2 = fma(ua[a], ua[a], un2);
-        y[a] = -g;
-    }
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-        double s = y[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) s = fma(-Lp[tri_idx(i, k)], y[k], s);
-        y[i] = s * Lp[tri_idx(i, i)];
-    }
-#pragma unroll
-    for (int i = n - 1; i >= 0; --i) {
-        double s = y[i];
-#pragma unroll
-        for (int k = i + 1; k < n; ++k) s = fma(-Lp[tri_idx(k, i)], y[k], s);
-        y[i] = s * Lp[tri_idx(i, i)];
-    }
-    double gd = 0.0;
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-        S.dir[off + a] = y[a];
-        gd = fma(V[a] - ua[a], y[a], gd);
-    }
-    int iters = S.iters[cell];
-    if (ph == PH_NEWTON) ++iters;
-    S.iters[cell] = iters;
-    const double gn = sqrt(gn2);
-    if (gn <= np.tau * sqrt(un2)) {
-        S.phase[cell] = PH_DONE;
-        return false;
-    }
-    if (iters >= np.max_iter) {
-        fail_t(KITRT_ENOCONVERGE);
-        return false;
-    }
-    if (mixed && ph == PH_NEWTON && gn > kStallRatio * S.gnorm[cell]) S.h64[cell] = 1;
-    if (S.gnorm) S.gnorm[cell] = gn;
-    S.gd[cell] = gd;
-    S.lam[cell] = 1.0;
-    S.halv[cell] = 0;
-    S.phase[cell] = PH_NEWTON;
-    return true;
-}
+#define KITRT_PT_NAME newton_post_thread
+#define KITRT_PT_UNROLL _Pragma("unroll")
+#include "newton_post_thread_body.cuh"
+#undef KITRT_PT_NAME
+#undef KITRT_PT_UNROLL
+#define KITRT_PT_NAME newton_post_thread_rolled
+#define KITRT_PT_UNROLL _Pragma("unroll 1")
+#include "newton_post_thread_body.cuh"
+#undef KITRT_PT_NAME
+#undef KITRT_PT_UNROLL
 
 // Newton logic of every listed cell after a round of sweeps: thread per list slot, reading (and
 // clearing) the slot's moment row. Counters (evaluations, largest count) are warp-aggregated.
@@ -391,7 +260,10 @@ post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k,
         if (it < cnt_in) {
             cell = list_in[it];
             double *row = Vacc + (size_t)it * n2;
-            cont = newton_post_thread<NN>(T, S, np, cell, row, u, mixed != 0, ev);
+            if constexpr (NN <= 3)
+                cont = newton_post_thread<NN>(T, S, np, cell, row, u, mixed != 0, ev);
+            else
+                cont = newton_post_thread_rolled<NN>(T, S, np, cell, row, u, mixed != 0, ev);
 #pragma unroll
             for (int c = 0; c < n2; ++c) row[c] = 0.0;
         }

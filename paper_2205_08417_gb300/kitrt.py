@@ -91,6 +91,8 @@ SIGNATURES = {
     "kitrt_mn_set_mlp": (C.c_int32, [_vp, _vp, _vp, C.c_int32, _vp]),
     "kitrt_vmf_moments": (C.c_int32, [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp]),
     "kitrt_closure_noalloc": (C.c_int32, [_vp, _vp, _vp, _vp, C.c_int32, _vp]),
+    "kitrt_sn_step": (C.c_int32, [_vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, _dp, C.c_double,
+                                  C.c_int32, _vp]),
     "kitrt_profile_enable": (C.c_int32, [_vp, C.c_int32]),
     "kitrt_profile_read": (C.c_int32, [_vp, C.POINTER(ProfileEntry), C.c_int32, _ip]),
 }
@@ -285,6 +287,28 @@ class MNSolver:
                                           int(u.shape[0]), _stream())
         if check:
             _check(rc, "kitrt_closure_noalloc")
+        return rc
+
+    def sn_step(self, psi, work, sigma_a, sigma_s, q, dt: float = 0.0, nsteps: int = 1, g=None,
+                check: bool = True):
+        """nsteps S_N steps of the ordinates psi [C, Q'] (float64 or float32 CUDA tensor) in
+        place; work is scratch of the same shape and dtype. g: per-degree scattering coefficients
+        (length N+1, g[0] = 1) or None for isotropic scattering."""
+        import torch
+        if psi.dtype not in (torch.float32, torch.float64) or work.dtype != psi.dtype:
+            raise ValueError("psi and work must share a float32 or float64 dtype")
+        if tuple(psi.shape) != (self.mesh.ncells, self.Qf) or work.shape != psi.shape:
+            raise ValueError("psi and work must be [ncells, Q'] (folded quadrature points)")
+        gp = None
+        if g is not None:
+            g = np.ascontiguousarray(g, dtype=np.float64)
+            gp = _np_d(g)
+        rc = _lib().kitrt_sn_step(self.handle, _dev(psi), _dev(work),
+                                  int(psi.dtype == torch.float32), _dev(sigma_a, torch.float64),
+                                  _dev(sigma_s, torch.float64), _dev(q, torch.float64), gp,
+                                  float(dt), int(nsteps), _stream())
+        if check:
+            _check(rc, "kitrt_sn_step")
         return rc
 
     def hessian(self, alpha):
