@@ -273,7 +273,12 @@ def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None)
     return out
 
 
-def run_sn(K, torch, W, steps, warmup, fp32, hbm_peak):
+# DRAM bytes (read + write) per launch of the S_N step from one ncu capture of the bench's own
+# launches (profiles/sn_tile_kernel_m3_line_source_100k.md); other workloads have no capture.
+SN_TRAFFIC = {("m3_line_source_100k", True): 286.9e6}
+
+
+def run_sn(K, torch, W, steps, warmup, fp32, hbm_peak, workload):
     """S_N steps (the nodal system with isotropic scattering) on the same mesh, quadrature and
     line-source start: ordinates psi = Phi / (4 pi) at the folded points, [C x Q'] resident on the
     device, double-buffered. Roofline: algorithmic bytes per cell = own row read + written
@@ -308,7 +313,8 @@ def run_sn(K, torch, W, steps, warmup, fp32, hbm_peak):
     out = {"cell_updates_per_s": C * steps / (ms / 1e3), "ms_per_step": ms / steps,
            "dtype": "f32" if fp32 else "f64", "scattering": "isotropic",
            "roofline": {"kernel": "sn_step", "bound": "hbm", "achieved": gbs, "peak": hbm_peak,
-                        "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+                        "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "traffic": SN_TRAFFIC.get((workload, fp32)),
                         "bytes_per_cell": per_cell, "avg_launch_ms": launch_ms,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
     if not fp32:
@@ -396,8 +402,8 @@ def main():
     sn = None
     if not args.no_sn:
         hp = hbm_peak_gbs()
-        sn = {"sn_fp32": run_sn(K, torch, W, args.steps, args.warmup, True, hp),
-              "sn_fp64": run_sn(K, torch, W, args.steps, args.warmup, False, hp)}
+        sn = {"sn_fp32": run_sn(K, torch, W, args.steps, args.warmup, True, hp, args.workload),
+              "sn_fp64": run_sn(K, torch, W, args.steps, args.warmup, False, hp, args.workload)}
     head = results[args.mode]
     if world > 1:
         ms, e2e_ms = max_over_ranks([head["ms"], head.get("e2e_ms", float("nan"))], "cuda")
