@@ -130,17 +130,84 @@ predict_kernel(NewtonState S, const double *__restrict__ u, NewtonParams np)
     }
 }
 
+// Thread-per-cell version of predict_kernel for N <= 3 (the packed factor fits in registers):
+// every FP64 instruction of the triangular solves keeps all 32 lanes busy.
+template <int NN>
+__global__ void __launch_bounds__(256)
+predict_thread_kernel(NewtonState S, const double *__restrict__ u, NewtonParams np)
+{
+    constexpr int n = Dims<NN>::n, npairs = Dims<NN>::npairs;
+    const int cnt = S.cnt[8];
+    const int stride = gridDim.x * blockDim.x;
+    const int rounds = (cnt + stride - 1) / stride;
+    for (int rd = 0; rd < rounds; ++rd) {
+        const int it = rd * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        bool cont = false;
+        int cell = -1;
+        if (it < cnt) {
+            cell = S.list[1][it];
+            const size_t off = (size_t)cell * n;
+            double Lp[npairs], y[n], g[n];
+            double gn2 = 0.0, un2 = 0.0, au = 0.0;
+#pragma unroll
+            for (int p = 0; p < npairs; ++p) Lp[p] = S.L[(size_t)cell * npairs + p];
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                const double ua = u[off + a];
+                g[a] = S.U[off + a] - ua;
+                gn2 = fma(g[a], g[a], gn2);
+                un2 = fma(ua, ua, un2);
+                au = fma(S.alpha[off + a], ua, au);
+                y[a] = -g[a];
+            }
+            // d = -H^-1 g with the stored factor (1/L_jj on its diagonal)
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+                double t = y[i];
+#pragma unroll
+                for (int k = 0; k < i; ++k) t = fma(-Lp[tri_idx(i, k)], y[k], t);
+                y[i] = t * Lp[tri_idx(i, i)];
+            }
+#pragma unroll
+            for (int i = n - 1; i >= 0; --i) {
+                double t = y[i];
+#pragma unroll
+                for (int k = i + 1; k < n; ++k) t = fma(-Lp[tri_idx(k, i)], y[k], t);
+                y[i] = t * Lp[tri_idx(i, i)];
+            }
+            double gd = 0.0;
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                S.dir[off + a] = y[a];
+                gd = fma(g[a], y[a], gd);
+            }
+            if (sqrt(gn2) <= np.tau * sqrt(un2)) {
+                S.phase[cell] = PH_DONE;  // converged; d is the polish step
+            } else {
+                if (S.gnorm) S.gnorm[cell] = sqrt(gn2);
+                S.f0[cell] = S.fsum[cell] - au;
+                S.gd[cell] = gd;
+                S.lam[cell] = 1.0;
+                S.phase[cell] = PH_NEWTON;
+                cont = true;
+            }
+        }
+        push_agg(S.list[0], &S.cnt[0], cell, cont);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // eval: one trial point per listed cell (alpha + lam dir, or alpha itself for PH_INIT), then the
 // Armijo decision, and on acceptance the Hessian, its Cholesky factor, the convergence test and
 // the next Newton direction.
 // ---------------------------------------------------------------------------------------------
 // FUSED: the warp also runs the per-cell Newton logic (used by the allocation-free closure);
-// otherwise the sweep writes the cell's moment row to Vacc[list slot] for the post kernel.
+// otherwise the sweep writes the cell's moments to column `list slot` of Vacc [n2 x C] for the
+// post kernel.
 template <int NN, bool FILTER, bool FUSED>
 __global__ void __launch_bounds__(kWarps * 32)
 eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
-            float *__restrict__ psi32, double *__restrict__ Vacc)
+            float *__restrict__ psi32, double *__restrict__ Vacc, int vs)
 {
     constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2;
     __shared__ double sH[kWarps][n * n];
@@ -193,7 +260,7 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
         if (!FUSED) {
 #pragma unroll
             for (int c = 0; c < n2; ++c)
-                if (lane == (c & 31)) Vacc[(size_t)it * n2 + c] = V[c];
+                if (lane == (c & 31)) Vacc[(size_t)c * vs + it] = V[c];
             continue;
         }
         __syncwarp();
@@ -331,6 +398,21 @@ int grid_for(const kitrt_mn *mn, int C, int per_sm)
     return need < cap ? (need > 0 ? need : 1) : cap;
 }
 
+// The predictor: thread per cell while the packed factor fits in registers (N <= 3), else warp
+// per cell with the factor in shared memory.
+template <int NN>
+void predict_launch(kitrt_mn *mn, const NewtonState &S, int C, const double *u, NewtonParams np,
+                    cudaStream_t s)
+{
+    if constexpr (NN <= 3) {
+        int tb = (C + 255) / 256;
+        if (tb > mn->nsm * 8) tb = mn->nsm * 8;
+        predict_thread_kernel<NN><<<tb > 0 ? tb : 1, 256, 0, s>>>(S, u, np);
+    } else {
+        predict_kernel<NN><<<grid_for(mn, C, 8), kWarps * 32, 0, s>>>(S, u, np);
+    }
+}
+
 }  // namespace
 
 #define KITRT_DISPATCH_N(N, ...)                        \
@@ -357,7 +439,7 @@ int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, cons
     if (blocks > mn->nsm * 8) blocks = mn->nsm * 8;
     LaunchScope ls(mn, PK_POST, s, 0);
     const int mixed = mn->p.mode != KITRT_FP64;
-    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(T, S, u, k, np, Vacc, mixed));
+    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(T, S, u, k, np, Vacc, mn->mesh->C, mixed));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
@@ -399,9 +481,8 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
         if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
     }
     if (first || learned) return KITRT_OK;
-    const int grid = grid_for(mn, C, 8);
     LaunchScope ls(mn, PK_BEGIN, s, 0);
-    KITRT_DISPATCH_N(mn->N, predict_kernel<NN><<<grid, kWarps * 32, 0, s>>>(S, u, np));
+    KITRT_DISPATCH_N(mn->N, predict_launch<NN>(mn, S, C, u, np, s));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
@@ -412,11 +493,12 @@ int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
     const int grid = grid_for(mn, C, 4);
     LaunchScope ls(mn, PK_EVAL, s, 0);
     if (!Vacc) {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false, true><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc)));
+        // fused sweep: no accumulator (the caller may pass a launch-only view without a mesh)
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false, true><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc, 0)));
     } else if (filter) {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc)));
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc, mn->mesh->C)));
     } else {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc)));
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc, mn->mesh->C)));
     }
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }

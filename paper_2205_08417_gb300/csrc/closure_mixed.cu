@@ -193,11 +193,14 @@ struct MixedSmem {
 // Work item = (tile of 128 listed cells, range of quadrature chunks). When few cells are listed
 // (the later sweeps of a closure), each tile's quadrature range is split over several CTAs so
 // that every SM gets work; the partial moments of a work item are added into Vacc (one FP64 row
-// of n2 moments per list position) with atomics, and mixed_post_kernel finishes the Newton logic.
+// of n2 moments per list position: entry c of slot j at Vacc[c vs_c + j vs_s], [n2 x C] columns
+// for the Newton sweeps, [C x n2] rows for the moments of given alphas) with atomics, and the
+// post kernel finishes the Newton logic.
 template <int NN, bool BF16, bool MOMENTS_ONLY>
 __global__ void __launch_bounds__(kThreads, 1)
 eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
-                  const double *__restrict__ alpha_in, double *__restrict__ Vacc, int C,
+                  const double *__restrict__ alpha_in, double *__restrict__ Vacc, int vs_c, int vs_s,
+                  int C,
                   int target_items, float *__restrict__ psi32)
 {
     using D = MixedDims<NN>;
@@ -365,13 +368,13 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
         // partial moments of this work item into the accumulator row of its list position: the
         // FP64 gradient moments from both halves, the tensor-core moments from TMEM (warps 0-3)
         if (r < rows && (MOMENTS_ONLY || active)) {
-            double *row = Vacc + (size_t)(base + r) * n2;
+            double *row = Vacc + (size_t)(base + r) * vs_s;
 #pragma unroll
-            for (int a = 0; a < n; ++a) atomicAdd(row + a, U[a]);
+            for (int a = 0; a < n; ++a) atomicAdd(row + (size_t)a * vs_c, U[a]);
         }
         if (h == 0) {
             const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-            double *row = Vacc + (size_t)(base + r) * n2;
+            double *row = Vacc + (size_t)(base + r) * vs_s;
 #pragma unroll
             for (int c0 = 0; c0 < NP; c0 += 16) {
                 float v[16];
@@ -379,7 +382,7 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                 if (r < rows && (MOMENTS_ONLY || active)) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
-                        if (c0 + i < n2 - n) atomicAdd(row + n + c0 + i, (double)v[i]);
+                        if (c0 + i < n2 - n) atomicAdd(row + (size_t)(n + c0 + i) * vs_c, (double)v[i]);
                 }
             }
         }
@@ -419,7 +422,8 @@ int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const
     const int grid = tiles < mn->nsm ? (tiles > 0 ? tiles : 1) : mn->nsm;
     const int target = 2 * mn->nsm;
     eval_mixed_kernel<NN, BF16, MO><<<mn->nsm, kThreads, L::total, s>>>(
-        T, S, k, BF16 ? (const void *)mn->d_Mhi16 : (const void *)mn->d_Mhi32, alpha_in, Vacc, C, target,
+        T, S, k, BF16 ? (const void *)mn->d_Mhi16 : (const void *)mn->d_Mhi32, alpha_in, Vacc,
+        MO ? 1 : mn->mesh->C, MO ? Dims<NN>::n2 : 1, C, target,
         psi32);
     (void)grid;
     if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;

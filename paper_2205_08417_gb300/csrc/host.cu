@@ -623,7 +623,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
     // mixed sweeps accumulate moments per list slot; every slot is cleared by its consumer, but an
     // aborted closure could leave partial sums behind
     if (mn->d_Vacc)
-        CUDA_OK(cudaMemsetAsync(mn->d_Vacc, 0, sizeof(double) * (size_t)C * mn->n2, s));
+        CUDA_OK(cudaMemsetAsync(mn->d_Vacc, 0, sizeof(double) * (size_t)mn->mesh->C * mn->n2, s));
     int rc = launch_begin(mn, T, mn->st, C, u, alpha_in, first, np, s, learned);
     if (rc) return rc;
     if (learned) {

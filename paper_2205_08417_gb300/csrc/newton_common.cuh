@@ -244,7 +244,7 @@ __device__ __forceinline__ void push_agg(int32_t *list, int32_t *cnt, int cell, 
 template <int NN>
 __global__ void __launch_bounds__(256)
 post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
-                   double *__restrict__ Vacc, int mixed)
+                   double *__restrict__ Vacc, int vs, int mixed)
 {
     constexpr int n2 = Dims<NN>::n2;
     const int32_t *list_in = S.list[k & 1];
@@ -259,13 +259,15 @@ post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k,
         int cell = -1, ev = 0;
         if (it < cnt_in) {
             cell = list_in[it];
-            double *row = Vacc + (size_t)it * n2;
+            // the slot's moments are a column of the [n2 x vs] accumulator: consecutive slots
+            // (threads) read and clear consecutive addresses
+            double *row = Vacc + it;
             if constexpr (NN <= 3)
-                cont = newton_post_thread<NN>(T, S, np, cell, row, u, mixed != 0, ev);
+                cont = newton_post_thread<NN>(T, S, np, cell, row, vs, u, mixed != 0, ev);
             else
-                cont = newton_post_thread_rolled<NN>(T, S, np, cell, row, u, mixed != 0, ev);
+                cont = newton_post_thread_rolled<NN>(T, S, np, cell, row, vs, u, mixed != 0, ev);
 #pragma unroll
-            for (int c = 0; c < n2; ++c) row[c] = 0.0;
+            for (int c = 0; c < n2; ++c) row[(size_t)c * vs] = 0.0;
         }
         // every slot taken in this round is one evaluation
         const unsigned act = __activemask();

@@ -3,13 +3,13 @@
 // loops rolled (N >= 4: the 120 or 231 factor entries live in local memory; full unrolling
 // would spill anyway and takes the compiler minutes). The includer defines KITRT_PT_NAME and
 // KITRT_PT_UNROLL. No include guard on purpose.
-// One-thread version of newton_post for the scalar Newton logic after an evaluation: V is the
-// cell's row of n2 degree-2N moments (global memory). Every FP64 instruction of this logic keeps
+// One-thread version of newton_post for the scalar Newton logic after an evaluation: V points to
+// the cell's n2 degree-2N moments in global memory, entry c at V[c vs]. Every FP64 instruction of this logic keeps
 // all 32 lanes busy (32 cells per warp), which matters on a GPU whose FP64 pipe is narrow.
 // Returns true when the cell continues (must be appended to the next list).
 template <int NN>
 __device__ bool KITRT_PT_NAME(const Tables &T, const NewtonState &S, const NewtonParams &np,
-                                   int cell, const double *__restrict__ V,
+                                   int cell, const double *__restrict__ V, int vs,
                                    const double *__restrict__ u, bool mixed, int &evals_out)
 {
     constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2, npairs = Dims<NN>::npairs;
@@ -27,7 +27,7 @@ KITRT_PT_UNROLL
     }
     bool finite = true;
 KITRT_PT_UNROLL
-    for (int c = 0; c < n2; ++c) finite = finite && isfinite(V[c]);
+    for (int c = 0; c < n2; ++c) finite = finite && isfinite(V[(size_t)c * vs]);
     const double fs = V[0] / T.m0;
     const double ft = fs - au;
     const int ev = S.evals[cell] + 1;
@@ -73,7 +73,7 @@ KITRT_PT_UNROLL
 KITRT_PT_UNROLL
     for (int p = 0; p < npairs; ++p) {
         double h = 0.0;
-        for (int t = T.gstart[p]; t < T.gstart[p + 1]; ++t) h = fma(T.gcoef[t], V[T.gidx[t]], h);
+        for (int t = T.gstart[p]; t < T.gstart[p + 1]; ++t) h = fma(T.gcoef[t], V[(size_t)T.gidx[t] * vs], h);
         Lp[p] = h;
     }
     bool spd = true;
@@ -104,7 +104,7 @@ KITRT_PT_UNROLL
 KITRT_PT_UNROLL
     for (int a = 0; a < n; ++a) {
         S.alpha[off + a] = at[a];
-        S.U[off + a] = V[a];
+        S.U[off + a] = V[(size_t)a * vs];
     }
     S.fsum[cell] = fs;
     S.f0[cell] = ft;
@@ -115,7 +115,7 @@ KITRT_PT_UNROLL
     double gn2 = 0.0, un2 = 0.0;
 KITRT_PT_UNROLL
     for (int a = 0; a < n; ++a) {
-        const double g = V[a] - ua[a];
+        const double g = V[(size_t)a * vs] - ua[a];
         gn2 = fma(g, g, gn2);
         un2 = fma(ua[a], ua[a], un2);
         y[a] = -g;
@@ -138,7 +138,7 @@ KITRT_PT_UNROLL
 KITRT_PT_UNROLL
     for (int a = 0; a < n; ++a) {
         S.dir[off + a] = y[a];
-        gd = fma(V[a] - ua[a], y[a], gd);
+        gd = fma(V[(size_t)a * vs] - ua[a], y[a], gd);
     }
     int iters = S.iters[cell];
     if (ph == PH_NEWTON) ++iters;
