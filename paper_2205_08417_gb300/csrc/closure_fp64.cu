@@ -21,6 +21,7 @@ namespace {
 
 using namespace kitrt_dev;
 constexpr int kWarps = 8;  // warps per block
+constexpr int kThreadBlock = 64;  // block of the thread-per-cell Newton kernels
 
 // ---------------------------------------------------------------------------------------------
 // begin: start a closure. first != 0: every cell starts from alpha_in with an evaluation.
@@ -405,9 +406,9 @@ void predict_launch(kitrt_mn *mn, const NewtonState &S, int C, const double *u, 
                     cudaStream_t s)
 {
     if constexpr (NN <= 3) {
-        int tb = (C + 255) / 256;
-        if (tb > mn->nsm * 8) tb = mn->nsm * 8;
-        predict_thread_kernel<NN><<<tb > 0 ? tb : 1, 256, 0, s>>>(S, u, np);
+        int tb = (C + kThreadBlock - 1) / kThreadBlock;
+        if (tb > mn->nsm * 32) tb = mn->nsm * 32;
+        predict_thread_kernel<NN><<<tb > 0 ? tb : 1, kThreadBlock, 0, s>>>(S, u, np);
     } else {
         predict_kernel<NN><<<grid_for(mn, C, 8), kWarps * 32, 0, s>>>(S, u, np);
     }
@@ -435,11 +436,13 @@ int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cud
 int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u, int k,
                 NewtonParams np, double *Vacc, cudaStream_t s)
 {
-    int blocks = (C + 255) / 256;
-    if (blocks > mn->nsm * 8) blocks = mn->nsm * 8;
+    // 64-thread blocks: the listed cells (often a few thousand) fill the low block indices, and
+    // small blocks spread them over every SM instead of a few
+    int blocks = (C + kThreadBlock - 1) / kThreadBlock;
+    if (blocks > mn->nsm * 32) blocks = mn->nsm * 32;
     LaunchScope ls(mn, PK_POST, s, 0);
     const int mixed = mn->p.mode != KITRT_FP64;
-    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(T, S, u, k, np, Vacc, mn->mesh->C, mixed));
+    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, kThreadBlock, 0, s>>>(T, S, u, k, np, Vacc, mn->mesh->C, mixed));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
