@@ -4,10 +4,12 @@
 //   k = nearest integer to x * 256 / ln2,  k = 256 m + j (0 <= j < 256),
 //   r = x - k ln2/256 (two-part constant, |r| <= ln2/512),
 //   exp(x) = 2^m * T_j * (1 + p(r)),  T_j = 2^(j/256) (table, correctly rounded),
-//   p(r) = r + r^2/2 + r^3/6 + r^4/24 + r^5/120 (truncation error below r^6/720 < 1e-20).
-// About ten FP64-pipe instructions; the scaling by 2^m is an integer add to the exponent field.
-// Arguments below -707 return 0 (the true value is below 1e-307, a weight no sum here can see),
-// above 709.78 return +inf, and NaN propagates.
+//   p(r) = r + r^2/2 + r^3/6 + r^4/24 (truncation error below r^5/120 < 4e-17, a third of an
+//   ulp, for |r| <= ln2/512).
+// Nine FP64-pipe instructions on the common path; the scaling by 2^m is an integer add to the
+// exponent field, and the range test reads the high word as an integer. Arguments below -707
+// return 0 (the true value is below 1e-307, a weight no sum here can see), above 709.78 return
+// +inf, and NaN propagates.
 #pragma once
 
 namespace kitrt_dev {
@@ -18,15 +20,19 @@ __device__ __forceinline__ double kexp(double x, const double *__restrict__ tab)
     const double kL1 = 0.0027076061740622863;         // ln2/256, leading part
     const double kL2 = 9.058776616587108e-20;         // ln2/256 - kL1
     const double kShift = 6755399441055744.0;         // 1.5 * 2^52: rounds to an integer
-    if (!(x > -707.0)) return x != x ? x : 0.0;
-    if (x > 709.78) return __longlong_as_double(0x7ff0000000000000LL);
+    // |x| < 512 is tested on the high word in integer arithmetic (the FP64 pipe is the narrow
+    // resource); only the rare rest is compared in FP64
+    if ((__double2hiint(x) & 0x7fffffff) >= 0x40800000) {
+        if (!(x > -707.0)) return x != x ? x : 0.0;
+        if (x > 709.78) return __longlong_as_double(0x7ff0000000000000LL);
+    }
     const double t = fma(x, kInvL, kShift);
     const int k = __double2loint(t);
     const double kf = t - kShift;
     double r = fma(-kf, kL1, x);
     r = fma(-kf, kL2, r);
-    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    p = fma(r, p, 1.0 / 6.0);
+    // 1 + p(r) = exp(r) to degree 4: the truncation r^5/120 < 4e-17 for |r| <= ln2/512
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     p = fma(r, p, 0.5);
     p = fma(r * r, p, r);
     const double Tj = __ldg(tab + (k & 255));
