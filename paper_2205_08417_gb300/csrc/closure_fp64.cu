@@ -438,11 +438,11 @@ int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, cons
 {
     // 64-thread blocks: the listed cells (often a few thousand) fill the low block indices, and
     // small blocks spread them over every SM instead of a few
-    int blocks = (C + kThreadBlock - 1) / kThreadBlock;
+    int blocks = (C + kPostBlock - 1) / kPostBlock;
     if (blocks > mn->nsm * 32) blocks = mn->nsm * 32;
     LaunchScope ls(mn, PK_POST, s, 0);
     const int mixed = mn->p.mode != KITRT_FP64;
-    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, kThreadBlock, 0, s>>>(T, S, u, k, np, Vacc, mn->mesh->C, mixed));
+    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, kPostBlock, 0, s>>>(T, S, u, k, np, Vacc, mn->mesh->C, mixed));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 

@@ -241,12 +241,16 @@ __device__ __forceinline__ void push_agg(int32_t *list, int32_t *cnt, int cell, 
 
 // Newton logic of every listed cell after a round of sweeps: thread per list slot, reading (and
 // clearing) the slot's moment row. Counters (evaluations, largest count) are warp-aggregated.
+// The slot's n2 moments are first copied to shared memory (all loads in flight together), where
+// the Hessian assembly's table-driven reads then find them at shared-memory latency.
+constexpr int kPostBlock = 64;
 template <int NN>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPostBlock)
 post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
                    double *__restrict__ Vacc, int vs, int mixed)
 {
     constexpr int n2 = Dims<NN>::n2;
+    __shared__ double sV[n2 * kPostBlock];  // [n2][thread]
     const int32_t *list_in = S.list[k & 1];
     int32_t *list_out = S.list[(k + 1) & 1];
     const int cnt_in = S.cnt[k % 3];
@@ -262,12 +266,15 @@ post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k,
             // the slot's moments are a column of the [n2 x vs] accumulator: consecutive slots
             // (threads) read and clear consecutive addresses
             double *row = Vacc + it;
-            if constexpr (NN <= 3)
-                cont = newton_post_thread<NN>(T, S, np, cell, row, vs, u, mixed != 0, ev);
-            else
-                cont = newton_post_thread_rolled<NN>(T, S, np, cell, row, vs, u, mixed != 0, ev);
+            double *mine = sV + threadIdx.x;
+#pragma unroll
+            for (int c = 0; c < n2; ++c) mine[c * kPostBlock] = row[(size_t)c * vs];
 #pragma unroll
             for (int c = 0; c < n2; ++c) row[(size_t)c * vs] = 0.0;
+            if constexpr (NN <= 3)
+                cont = newton_post_thread<NN>(T, S, np, cell, mine, kPostBlock, u, mixed != 0, ev);
+            else
+                cont = newton_post_thread_rolled<NN>(T, S, np, cell, mine, kPostBlock, u, mixed != 0, ev);
         }
         // every slot taken in this round is one evaluation
         const unsigned act = __activemask();

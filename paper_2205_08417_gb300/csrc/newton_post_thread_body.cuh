@@ -4,8 +4,9 @@
 // would spill anyway and takes the compiler minutes). The includer defines KITRT_PT_NAME and
 // KITRT_PT_UNROLL. No include guard on purpose.
 // One-thread version of newton_post for the scalar Newton logic after an evaluation: V points to
-// the cell's n2 degree-2N moments in global memory, entry c at V[c vs]. Every FP64 instruction of this logic keeps
-// all 32 lanes busy (32 cells per warp), which matters on a GPU whose FP64 pipe is narrow.
+// the cell's n2 degree-2N moments (the post kernel's shared-memory copy), entry c at V[c vs].
+// Every FP64 instruction of this logic keeps all 32 lanes busy (32 cells per warp), which
+// matters on a GPU whose FP64 pipe is narrow.
 // Returns true when the cell continues (must be appended to the next list).
 template <int NN>
 __device__ bool KITRT_PT_NAME(const Tables &T, const NewtonState &S, const NewtonParams &np,
