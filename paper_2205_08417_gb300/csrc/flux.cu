@@ -77,7 +77,7 @@ flux_update_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restr
 }
 
 // FP32 variant for the mixed modes: FP32 ansatz and upwind sums, Kahan-compensated FP32
-// projection per lane, a compensated (two-sum) FP32 butterfly across the warp, and the FP64
+// projection per lane, a compensated (two-sum) FP32 reduce-scatter across the warp, and the FP64
 // update applied afterwards with every lane busy. A warp takes a batch of kBatch consecutive cells:
 // their flux moments go to shared memory, then the warp updates all (cell, moment) pairs of the
 // batch (FP64 instructions on a partly idle warp cost as much as on a full one).
@@ -86,6 +86,56 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     s = a + b;
     const float bp = s - a;
     e = (a - (s - bp)) + (b - bp);
+}
+
+// Compensated reduce-scatter of n per-lane sums (F - Fc) across the warp. The sums are padded to
+// S slots (the next power of two >= n). At each of the log2(S) halving levels (offsets 16, 8, ...)
+// a lane keeps one half of its slots, sends the other half to its partner and adds the partner's
+// copy of the kept half with a two-sum; the remaining levels are compensated butterflies between
+// lanes holding the same slot. Lane L ends with the total of slot L >> (5 - log2 S) (value s + e);
+// every lane whose low 5 - log2 S bits are zero holds a distinct slot. That is S - 1 two-sums per
+// lane (plus 5 - log2 S for the butterflies) instead of 5 n for a butterfly per sum.
+template <int n>
+__device__ __forceinline__ int warp_reduce_scatter(const float (&F)[n], const float (&Fc)[n], int lane,
+                                                   float &rs, float &re)
+{
+    constexpr int S = n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+    constexpr int H = S == 1 ? 0 : S == 2 ? 1 : S == 4 ? 2 : S == 8 ? 3 : S == 16 ? 4 : 5;
+    float sv[S], ev[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        sv[k] = k < n ? F[k < n ? k : 0] : 0.0f;
+        ev[k] = k < n ? -Fc[k < n ? k : 0] : 0.0f;
+    }
+#pragma unroll
+    for (int lvl = 0; lvl < H; ++lvl) {
+        const int o = 16 >> lvl;
+        const int half = S >> (lvl + 1);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const float ks = upper ? sv[k + half] : sv[k], ke = upper ? ev[k + half] : ev[k];
+            const float xs = upper ? sv[k] : sv[k + half], xe = upper ? ev[k] : ev[k + half];
+            const float ps = __shfl_xor_sync(kFull, xs, o), pe = __shfl_xor_sync(kFull, xe, o);
+            float t, e;
+            two_sum(ks, ps, t, e);
+            sv[k] = t;
+            ev[k] = ke + pe + e;
+        }
+    }
+    float s0 = sv[0], e0 = ev[0];
+#pragma unroll
+    for (int o = 16 >> H; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(kFull, s0, o), eo = __shfl_xor_sync(kFull, e0, o);
+        float t, e;
+        two_sum(s0, so, t, e);
+        s0 = t;
+        e0 = e0 + eo + e;
+    }
+    rs = s0;
+    re = e0;
+    // the lane's slot, or -1 for a lane that only duplicates another's slot
+    return (lane & ((1 << (5 - H)) - 1)) == 0 ? lane >> (5 - H) : -1;
 }
 
 template <int NN>
@@ -141,25 +191,10 @@ flux_update32_kernel(Tables T, const int4 *__restrict__ nbr, const double *__res
                     F[a] = t;
                 }
             }
-            // value = F - Fc per lane; butterfly with two-sum keeps the rounding errors
-            float mine_s = 0.0f, mine_e = 0.0f;
-#pragma unroll
-            for (int a = 0; a < n; ++a) {
-                float sv = F[a], ev = -Fc[a];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float so = __shfl_xor_sync(kFull, sv, o), eo = __shfl_xor_sync(kFull, ev, o);
-                    float t, e;
-                    two_sum(sv, so, t, e);
-                    sv = t;
-                    ev = ev + eo + e;
-                }
-                if (lane == a) {
-                    mine_s = sv;
-                    mine_e = ev;
-                }
-            }
-            if (lane < n) sF[wib][ci * n + lane] = (double)mine_s + (double)mine_e;
+            // value = F - Fc per lane; compensated reduce-scatter keeps the rounding errors
+            float rs, re;
+            const int slot = warp_reduce_scatter<n>(F, Fc, lane, rs, re);
+            if (slot >= 0 && slot < n) sF[wib][ci * n + slot] = (double)rs + (double)re;
         }
         __syncwarp();
         for (int idx = lane; idx < nb_cells * n; idx += 32) {
