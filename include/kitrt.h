@@ -192,6 +192,10 @@ int32_t kitrt_closure_batch(kitrt_mn *mn, const double *u, double *alpha, int32_
  * psi_cq = exp(alpha_c . m_q). */
 int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *stream);
 
+/* Forget the closure state kept for continuation (see kitrt_step): the next kitrt_step starts
+ * from the alpha it is given. */
+int32_t kitrt_mn_reset(kitrt_mn *mn);
+
 /* nsteps explicit M_N steps, in place:
  *   u^{n+1}_i = u^n_i - dt/A_i sum_{j in N(i)} F_up(psi_i, psi_j) + dt R_i(u^n_i),
  *   R_i(u) = -sigma_a,i u - sigma_s,i (u - u_0 e_0) + q_i <m>,
@@ -199,6 +203,13 @@ int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *strea
  * [Sec. 4.2 explicit iteration; Sec. 3.1: isotropic scattering is diagonal in the moments].
  *   u       device [C x n]: u^0 in, u^{nsteps} out.
  *   alpha   device [C x n]: warm start in; out: closure of u^{nsteps-1} (the last closed state).
+ *           When alpha is the same buffer as in the last successful kitrt_step on this solver
+ *           (or kitrt_closure in FP64 mode), and no kitrt_closure_batch, kitrt_adjoint or
+ *           kitrt_mn_reset came in between, the first step continues from the solver's own state
+ *           of that closure instead (the Newton predictor starts from the stored factor, as it
+ *           does between the steps of one call), so that stepping one call at a time costs what
+ *           one call of many steps costs; alpha is then output only. The result does not depend
+ *           on the start: every closure is solved to the same tolerance.
  *   sigma_a, sigma_s, q  device [C] per-cell absorption, scattering, isotropic source.
  *   dt      time step; dt <= 0 selects cfl * min_i 2 A_i / P_i. EINVAL when
  *           dt * max(sigma_a + sigma_s) > 1 is detectable on the host (not checked on device).

@@ -187,6 +187,7 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
                                  double dt, int32_t nsteps, int32_t ckpt_every, double *J,
                                  double *dJ_dsa, double *dJ_dss, void *stream)
 {
+    if (mn) mn->warm_alpha = nullptr;  // the adjoint's sweeps overwrite the closure state
     if (!mn || !u0 || !alpha0 || !sigma_a || !sigma_s || !q || !block_of_cell || !target || !J ||
         !dJ_dsa || !dJ_dss || nblocks < 1 || nsteps < 0 || ckpt_every < 1 || mn->p.mode != KITRT_FP64)
         return KITRT_EINVAL;

@@ -703,9 +703,13 @@ int32_t kitrt_closure_batch(kitrt_mn *mn, const double *u, double *alpha, int32_
     cudaStream_t s = (cudaStream_t)stream;
     if (stats) memset(stats, 0, sizeof(*stats));
     const int64_t launches0 = mn->launch_count;
+    mn->warm_alpha = nullptr;
     int rc = run_closure(mn, ncells, u, alpha, 1, s, stats);
     int rc2 = launch_finish(mn, mn->tables(), mn->st, ncells, alpha, nullptr, nullptr,
                             polish_of(mn), 0, s);
+    // a full-mesh closure leaves a state a following kitrt_step can continue from (a partial
+    // batch leaves the other cells' ansatz out of date)
+    if (!rc && !rc2 && ncells == mn->mesh->C && mn->p.mode == KITRT_FP64) mn->warm_alpha = alpha;
     if (status)
         CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * ncells,
                                 cudaMemcpyDeviceToDevice, s));
@@ -743,12 +747,17 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
     const int64_t launches0 = mn->launch_count;
     const int C = mn->mesh->C;
     const Tables T = mn->tables();
+    if (nsteps == 0) return KITRT_OK;
+    // the same alpha buffer as the last successful full-mesh closure: continue from the solver's
+    // own state (the Newton predictor starts from the stored factor); else start from alpha
+    const bool cont = mn->warm_alpha == alpha;
+    mn->warm_alpha = nullptr;
     int rc = KITRT_OK;
     for (int32_t it = 0; it < nsteps; ++it) {
         const bool fp64 = mn->p.mode == KITRT_FP64;
         // mixed modes: the evaluation sweeps write the FP32 ansatz of every accepted point, and
         // with no polish step the solution's ansatz is already in place
-        rc = run_closure(mn, C, u, alpha, it == 0, s, stats, fp64 ? nullptr : mn->d_psi32);
+        rc = run_closure(mn, C, u, alpha, it == 0 && !cont, s, stats, fp64 ? nullptr : mn->d_psi32);
         if (rc) break;
         rc = launch_finish(mn, T, mn->st, C, alpha, fp64 ? mn->d_psi : nullptr, nullptr,
                            polish_of(mn), it > 0, s);
@@ -757,6 +766,7 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
                                 u, sigma_a, sigma_s, q, dt, mn->p.bc, s);
         if (rc) break;
     }
+    if (!rc) mn->warm_alpha = alpha;
     if (status)
         CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * C,
                                 cudaMemcpyDeviceToDevice, s));
@@ -765,6 +775,13 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
         CUDA_OK(cudaStreamSynchronize(s));
     }
     return rc;
+}
+
+int32_t kitrt_mn_reset(kitrt_mn *mn)
+{
+    if (!mn) return KITRT_EINVAL;
+    mn->warm_alpha = nullptr;
+    return KITRT_OK;
 }
 
 int32_t kitrt_hessian(kitrt_mn *mn, const double *alpha, double *H, void *stream)

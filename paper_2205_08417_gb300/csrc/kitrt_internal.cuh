@@ -109,6 +109,9 @@ struct kitrt_mn {
     double *d_psi = nullptr;   // [C x Qp] FP64 ansatz
     float *d_psi32 = nullptr;  // [C x Qp] FP32 ansatz (mixed modes)
     int32_t *h_cnt = nullptr;  // pinned copy of st.cnt
+    // alpha buffer of the last successful full-mesh closure (kitrt_step, kitrt_closure): a
+    // kitrt_step given the same buffer continues from the solver's state (warm predictor)
+    const double *warm_alpha = nullptr;
     int32_t *d_sn_flag = nullptr;  // S_N step: device status (KITRT_ETIMEOUT on an expired wait)
     int32_t *h_sn_flag = nullptr;  // pinned copy
     void *d_sn_cell = nullptr;     // [C x 12] per-cell coefficients of the S_N step (FP32 or FP64)

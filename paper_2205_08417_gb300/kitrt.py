@@ -91,6 +91,7 @@ SIGNATURES = {
     "kitrt_mn_set_mlp": (C.c_int32, [_vp, _vp, _vp, C.c_int32, _vp]),
     "kitrt_vmf_moments": (C.c_int32, [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp]),
     "kitrt_closure_noalloc": (C.c_int32, [_vp, _vp, _vp, _vp, C.c_int32, _vp]),
+    "kitrt_mn_reset": (C.c_int32, [_vp]),
     "kitrt_sn_step": (C.c_int32, [_vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, _dp, C.c_double,
                                   C.c_int32, _vp]),
     "kitrt_profile_enable": (C.c_int32, [_vp, C.c_int32]),
@@ -338,6 +339,10 @@ class MNSolver:
         if check:
             _check(rc, "kitrt_step")
         return (rc, st.as_dict()) if stats else rc
+
+    def reset(self):
+        """Forget the closure state kept for continuation: the next step starts from its alpha."""
+        _check(_lib().kitrt_mn_reset(self.handle), "kitrt_mn_reset")
 
     def profile(self, on: bool = True):
         _check(_lib().kitrt_profile_enable(self.handle, int(on)), "kitrt_profile_enable")

@@ -297,3 +297,37 @@ def test_table_exp_against_reference_exp(K):
     assert rel.max() <= 2.0 ** -51, rel.max()
     assert (psi[~live, 0] == 0).all()
     assert np.all(psi == psi[:, :1])  # m_0 is constant: every point sees the same exponent
+
+
+def test_step_calls_continue_from_the_solver_state(K):
+    """Stepping one kitrt_step call at a time with the same alpha buffer continues from the
+    solver's closure state: the result is bitwise that of one call of all the steps, the continued
+    calls evaluate fewer cells than a cold first step, and kitrt_mn_reset (or another alpha
+    buffer) starts cold again with the same result to the closure tolerance."""
+    m = synth.jittered_mesh(45, -1.5, 1.5, seed=1)
+    mesh = K.Mesh(m.xy, m.tri)
+    C = mesh.ncells
+    s = K.MNSolver(mesh, 2, 10, tau=1e-10)
+    u0 = synth.isotropic_moments(synth.line_source_density(m.centroids()), s.n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sa, ss, q = dev(np.zeros(C)), dev(np.ones(C)), dev(np.zeros(C))
+    dt, nsteps = 0.4 * mesh.geometry()["min_inradius"], 8
+    ua = dev(u0)
+    aa = s.isotropic_alpha(ua)
+    s.step(ua, aa, sa, ss, q, dt=dt, nsteps=nsteps)
+    s.reset()
+    ub = dev(u0)
+    ab = s.isotropic_alpha(ub)
+    evals = []
+    for _ in range(nsteps):
+        _, st = s.step(ub, ab, sa, ss, q, dt=dt, nsteps=1, stats=True)
+        evals.append(st["evaluations"])
+    assert torch.equal(ua, ub) and torch.equal(aa, ab)
+    assert evals[0] >= C and max(evals[1:]) < evals[0]
+    # a continued step and a cold step from the same state reach the same closure to tolerance
+    ad = ab.clone()
+    uc, ud = ub.clone(), ub.clone()
+    s.step(uc, ab, sa, ss, q, dt=dt, nsteps=1)  # continues (same alpha buffer)
+    s.reset()
+    s.step(ud, ad, sa, ss, q, dt=dt, nsteps=1)  # cold, from the same alpha
+    assert (torch.linalg.norm(uc - ud) / torch.linalg.norm(uc)).item() <= 1e-12
