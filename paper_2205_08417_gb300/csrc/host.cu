@@ -532,6 +532,13 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
         if (p.mode == KITRT_LEARNED) TRY(dev_alloc(mn, &mn->d_alpha_nn, C * (size_t)n));
         TRY(dev_alloc(mn, &S.h64, C));
         TRY(dev_alloc(mn, &S.gnorm, C));
+        if (p.mode == KITRT_LEARNED) {
+            TRY(dev_alloc(mn, &S.lfac, C));
+            if (cudaMemset(S.lfac, 0, sizeof(int32_t) * C) != cudaSuccess) {
+                kitrt_mn_destroy(mn);
+                return KITRT_ECUDA;
+            }
+        }
     }
     if (cudaMallocHost(&mn->h_cnt, 16 * sizeof(int32_t)) != cudaSuccess) {
         kitrt_mn_destroy(mn);

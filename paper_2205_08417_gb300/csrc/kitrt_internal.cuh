@@ -59,6 +59,7 @@ struct NewtonState {
     int32_t *status;   // [C]
     int32_t *h64;      // [C] mixed modes: 1 = this cell evaluates its Hessian in FP64 (else NULL)
     double *gnorm;     // [C] mixed modes: ||g|| at the last accepted point (else NULL)
+    int32_t *lfac;     // [C] learned mode: 1 once S.L holds a factor of this cell (else NULL)
     int32_t *list[2];  // active cell lists (ping-pong)
     int32_t *cnt;      // [16]: cnt[0..2] rotating list counters, cnt[3] failures, cnt[4] max
                        //   evals, cnt[5] fallbacks, cnt[6] evaluations, cnt[7] timeout status,

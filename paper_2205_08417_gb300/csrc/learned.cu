@@ -6,7 +6,9 @@
 // density]: with z'_q = sum_{a>=1} alpha_a m_a(q) and U'_a = sum_q w_q exp(z'_q) m_a(q), the
 // choice exp(alpha_0 m_0) = u_0 / U'_0 makes the zeroth moment of exp(alpha.m) equal to u_0, and
 // every other moment is U_a = (u_0 / U'_0) U'_a. The cell keeps the network's answer when
-// ||U - u||_2 <= fallback_tol ||u||_2 (computed in FP64), otherwise Newton starts from it.
+// ||U - u||_2 <= fallback_tol ||u||_2 (computed in FP64); otherwise Newton starts from the better
+// (by dual objective) of that point and the previous closure's, the latter with a step from its
+// stored factor when the cell has one.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -25,7 +27,8 @@ learned_pass_kernel(Tables T, NewtonState S, const double *__restrict__ u,
                     const double *__restrict__ alpha_nn, double tol, float *__restrict__ psi32,
                     int first)
 {
-    constexpr int n = Dims<NN>::n;
+    constexpr int n = Dims<NN>::n, npairs = Dims<NN>::npairs;
+    __shared__ double sH[kWarps][n * n];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int Qp = T.Qp;
     const int count = S.cnt[8];
@@ -92,7 +95,29 @@ learned_pass_kernel(Tables T, NewtonState S, const double *__restrict__ u,
                 if (lane == 0) S.alpha[off] = alpha0;
                 if (lane >= 1 && lane < n) S.alpha[off + lane] = al;
             }
-            if (lane == 0) {
+            if (!use_nn && !first && S.lfac && S.lfac[cell]) {
+                // the previous closure's point is the better start, and its moments and a
+                // factor of this cell are stored: take the Newton step from them at once, as the
+                // predictor of the other modes does, instead of evaluating that point again
+                double *H = sH[wib];
+                const double ap = lane < n ? S.alpha[off + lane] : 0.0;
+                const double g = lane < n ? S.U[off + lane] - ua : 0.0;
+                for (int a = lane; a < n; a += 32)
+                    for (int b = 0; b <= a; ++b) H[a * n + b] = S.L[(size_t)cell * npairs + tri_idx(a, b)];
+                __syncwarp();
+                const double d = warp_chol_solve<n>(H, -g, lane);
+                __syncwarp();
+                const double gn2 = warp_sum(g * g), au = warp_sum(ap * ua), gd = warp_sum(g * d);
+                if (lane < n) S.dir[off + lane] = d;
+                if (lane == 0) {
+                    if (S.gnorm) S.gnorm[cell] = sqrt(gn2);
+                    S.f0[cell] = S.fsum[cell] - au;
+                    S.gd[cell] = gd;
+                    S.lam[cell] = 1.0;
+                    S.phase[cell] = PH_NEWTON;
+                    atomicAdd(&S.cnt[5], 1);
+                }
+            } else if (lane == 0) {
                 S.phase[cell] = PH_INIT;
                 atomicAdd(&S.cnt[5], 1);
             }

@@ -182,6 +182,7 @@ __device__ void newton_post(const Tables &T, const NewtonState &S, const NewtonP
     }
     for (int a = lane; a < n; a += 32)
         for (int b = 0; b <= a; ++b) S.L[(size_t)cell * npairs + tri_idx(a, b)] = H[a * n + b];
+    if (lane == 0 && S.lfac) S.lfac[cell] = 1;
     const double g = lane < n ? Ua - ua : 0.0;
     const double d = warp_chol_solve<n>(H, -g, lane);
     __syncwarp();

@@ -111,6 +111,7 @@ KITRT_PT_UNROLL
     S.f0[cell] = ft;
 KITRT_PT_UNROLL
     for (int p = 0; p < npairs; ++p) S.L[(size_t)cell * npairs + p] = Lp[p];
+    if (S.lfac) S.lfac[cell] = 1;
     // d = -H^-1 g
     double y[n];
     double gn2 = 0.0, un2 = 0.0;
