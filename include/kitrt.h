@@ -93,6 +93,8 @@ typedef struct {
     int64_t fallbacks;     /* KITRT_LEARNED: cells that needed Newton after the MLP */
     double dt;             /* time step used */
     int64_t launches;      /* CUDA kernels the library launched in this call */
+    int64_t restarts;      /* KITRT_LEARNED: fallbacks whose better start was the previous closure's
+                              point, stepped from its stored Cholesky factor without a new pass */
 } kitrt_stats;
 
 /* Per-kernel-kind trace record (see kitrt_profile_enable). `units` counts what one kind
@@ -130,9 +132,14 @@ int32_t kitrt_mesh_geometry(const kitrt_mesh *mesh, int32_t *ncells, double *min
                             double *area, double *perim, double *centroid, int32_t *nbr,
                             double *nrm);
 
-/* Create an M_N solver on a mesh: builds the folded quadrature, the basis tables and the
- * workspace for every cell of the mesh (device allocations, owned by the handle). The mesh must
- * outlive the solver. */
+/* Create an M_N solver on a mesh: builds the folded quadrature [Sec. 3.2, Eq.
+ * spherical-coordinatesProduct: tensorised Gauss-Legendre points in mu times equally spaced
+ * azimuths], the real spherical-harmonic basis at its points [Sec. 3.1: the modal basis of the
+ * moment system, here the functions even in mu], the Gaunt coefficients <m_a m_b m~_c> with which
+ * the closure assembles the Hessian of its dual, and the workspace for every cell of the mesh
+ * (device allocations, owned by the handle). The mesh must outlive the solver. EINVAL for a degree
+ * outside 1..5, quad_order < degree + 1 or > 64, tau <= 0, max_iter < 1, max_halvings < 0, or an
+ * unknown mode or boundary condition; ENOMEM when an allocation fails. */
 int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kitrt_mn **out);
 int32_t kitrt_mn_destroy(kitrt_mn *mn);
 
@@ -161,8 +168,12 @@ int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out);
  * [Q' x 2], basis values [Q' x nmom]. */
 int32_t kitrt_mn_quadrature(const kitrt_mn *mn, double *w, double *omega, double *m);
 
-/* Isotropic closed form of the closure: alpha_0 = ln(u_0 / (4 pi m_0)) / m_0, other components
- * 0 (m_0 = 1/sqrt(4 pi)). u, alpha: device [C x n]. */
+/* Isotropic closed form of the closure [Sec. 3.1, Eq. entropyOCP with the Maxwell-Boltzmann
+ * entropy, whose minimiser is psi = exp(alpha.m)]: for u = (u_0, 0, ..., 0) the constant
+ * psi = u_0 / (4 pi m_0) reproduces u (the other basis functions integrate to zero against a
+ * constant), so alpha_0 = ln(u_0 / (4 pi m_0)) / m_0 and the other components are 0
+ * (m_0 = 1/sqrt(4 pi)). Only u_0 of each row is read. u, alpha: device [C x n]; asynchronous on
+ * `stream`. A row with u_0 <= 0 gets a non-finite alpha_0 (the closure then reports it). */
 int32_t kitrt_isotropic_alpha(kitrt_mn *mn, const double *u, double *alpha, void *stream);
 
 /* Entropy closure [Sec. 3.1, Eq. entropyOCP] of every cell: alpha minimises
@@ -193,7 +204,7 @@ int32_t kitrt_closure_batch(kitrt_mn *mn, const double *u, double *alpha, int32_
 int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *stream);
 
 /* Forget the closure state kept for continuation (see kitrt_step): the next kitrt_step starts
- * from the alpha it is given. */
+ * every cell from the alpha it is given, whatever its contents. */
 int32_t kitrt_mn_reset(kitrt_mn *mn);
 
 /* nsteps explicit M_N steps, in place:
@@ -203,16 +214,21 @@ int32_t kitrt_mn_reset(kitrt_mn *mn);
  * [Sec. 4.2 explicit iteration; Sec. 3.1: isotropic scattering is diagonal in the moments].
  *   u       device [C x n]: u^0 in, u^{nsteps} out.
  *   alpha   device [C x n]: warm start in; out: closure of u^{nsteps-1} (the last closed state).
- *           When alpha is the same buffer as in the last successful kitrt_step on this solver
- *           (or kitrt_closure in FP64 mode), and no kitrt_closure_batch, kitrt_adjoint or
- *           kitrt_mn_reset came in between, the first step continues from the solver's own state
- *           of that closure instead (the Newton predictor starts from the stored factor, as it
- *           does between the steps of one call), so that stepping one call at a time costs what
- *           one call of many steps costs; alpha is then output only. The result does not depend
- *           on the start: every closure is solved to the same tolerance.
+ *           Continuation is decided per cell by content: a cell whose given alpha row is, bit for
+ *           bit, the alpha this solver returned for it from its last successful closure (and no
+ *           kitrt_mn_reset came since) continues from the solver's stored state of that closure
+ *           (the Newton predictor starts from the stored factor, as it does between the steps of
+ *           one call), so that stepping one call at a time costs what one call of many steps
+ *           costs. Every other cell, for instance one whose row the caller overwrote with a new
+ *           warm start, starts from its given row. The result does not depend on the start
+ *           beyond the closure tolerance: every closure is solved to the same tolerance.
  *   sigma_a, sigma_s, q  device [C] per-cell absorption, scattering, isotropic source.
- *   dt      time step; dt <= 0 selects cfl * min_i 2 A_i / P_i. EINVAL when
- *           dt * max(sigma_a + sigma_s) > 1 is detectable on the host (not checked on device).
+ *   dt      time step; dt <= 0 selects cfl * min_i 2 A_i / P_i. The step must keep the kinetic
+ *           update of every ordinate positive [Sec. 4.4: the updated moments must stay
+ *           realizable]: dt (P_i / (2 A_i) + sigma_a,i + sigma_s,i) <= 1 in every cell (the
+ *           cell-wise form of dt sigma_t,max <= 1 - CFL). The library tests this on the device
+ *           and returns KITRT_EINVAL, before u is touched, when a cell violates it or has a
+ *           negative or non-finite coefficient.
  *   status  device [C] or NULL: per-cell status of the last failed closure.
  * Synchronises with `stream` once per step (closure completion test). On a closure failure the
  * step stops before updating u with that closure and returns its status. */
@@ -222,11 +238,12 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
 
 /* Entropy closure of a batch of moment vectors without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot let the library allocate device
- * memory at call time (a framework whose pool allocator owns the free memory, code running while
- * a stream is captured, a service that must not grow after start-up) and whose batch is not the
- * solver's mesh. It runs the same Newton iteration as kitrt_closure with the solver's tables and
- * parameters, but keeps its per-cell Newton state in one static device array of 8 MiB that every
- * GPU loading the library holds until the process exits.
+ * memory at call time, for instance a framework whose pool allocator already owns the free device
+ * memory (a cudaMalloc would fail or force the pool to release memory), or a long-running service
+ * that must not grow its footprint after start-up, and whose batch is not the solver's mesh. It
+ * runs the same FP64 Newton iteration as kitrt_closure with the solver's tables and parameters,
+ * but keeps its per-cell Newton state in one static device array of 8 MiB that every GPU loading
+ * the library holds until the process exits.
  *   u      device [ncells x nmom], read only; alpha device [ncells x nmom], warm start in,
  *          solution out; status device [ncells] or NULL.
  *   ncells may not exceed floor(8 MiB / per-cell bytes), where a cell needs
@@ -235,8 +252,10 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
  *          KITRT_ESCRATCH before touching any memory.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture. Every call shares the
- * array and leaves its contents behind; calls that overlap on the GPU (other streams or host
- * threads) race on it. Synchronises with `stream` like kitrt_closure. */
+ * array and leaves its contents behind (the call clears the counters that must start at zero);
+ * calls that overlap on the GPU (other streams or host threads) race on it. The call synchronises
+ * with `stream` once every four Newton sweeps to test for completion (a 32-byte device-to-host
+ * read of the counters) and, after a failure, to find the first failing cell. */
 int32_t kitrt_closure_noalloc(const kitrt_mn *mn, const double *u, double *alpha,
                               int32_t *status, int32_t ncells, void *stream);
 
@@ -277,10 +296,12 @@ int32_t kitrt_sn_step(kitrt_mn *mn, void *psi, void *work, int32_t fp32, const d
  *   target           device [C] uint8 (1 = cell in the target region).
  *   dt               time step (<= 0: cfl * min 2A/P); nsteps steps; ckpt_every >= 1 steps per
  *                    checkpoint segment (states are recomputed forward inside a segment).
- *   J                device [1]; dJ_dsa, dJ_dss device [nblocks] (overwritten).
- * Allocates checkpoint and segment buffers on the device for the duration of the call (about
- * (nsteps/ckpt_every + 2 ckpt_every + 4) C n doubles + C Q' doubles) and synchronises with
- * `stream` before returning. */
+ *   J                host [1]; dJ_dsa, dJ_dss host [nblocks] (overwritten).
+ * The first call (or one needing more than the last) allocates the checkpoint and segment buffers
+ * in the solver's workspace (about (nsteps/ckpt_every + 2 ckpt_every + 4) C n doubles + C Q'
+ * doubles); later calls reuse them and allocate nothing; kitrt_mn_destroy frees them. Checks the
+ * stability condition of kitrt_step (KITRT_EINVAL) and synchronises with `stream` before
+ * returning. */
 int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *alpha0, const double *sigma_a,
                       const double *sigma_s, const double *q, const int32_t *block_of_cell,
                       int32_t nblocks, const uint8_t *target, double dt, int32_t nsteps,

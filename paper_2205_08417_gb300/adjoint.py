@@ -19,8 +19,9 @@ class AbsorbedEnergy(torch.autograd.Function):
         ss = sigma_s_blk.detach()[block_of_cell.long()].contiguous()
         J, gsa, gss = solver.adjoint(u0, alpha0, sa, ss, q, block_of_cell, sigma_a_blk.numel(), target,
                                      dt, nsteps, ckpt_every)
-        ctx.save_for_backward(gsa, gss)
-        return J[0]
+        dev = sigma_a_blk.device
+        ctx.save_for_backward(torch.from_numpy(gsa).to(dev), torch.from_numpy(gss).to(dev))
+        return torch.tensor(J, dtype=torch.float64, device=dev)
 
     @staticmethod
     def backward(ctx, gJ):

@@ -180,6 +180,8 @@ adjoint_cell_kernel(Tables T, const int4 *__restrict__ nbr, const double *__rest
 // Declared in host.cu.
 int kitrt_internal_step(kitrt_mn *mn, double *u, double *alpha, const double *sa, const double *ss,
                         const double *q, double dt, int first, cudaStream_t s);
+int check_stability(kitrt_mn *mn, const double *sa, const double *ss, double dt, cudaStream_t s,
+                    bool wait);
 
 extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *alpha0,
                                  const double *sigma_a, const double *sigma_s, const double *q,
@@ -187,7 +189,6 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
                                  double dt, int32_t nsteps, int32_t ckpt_every, double *J,
                                  double *dJ_dsa, double *dJ_dss, void *stream)
 {
-    if (mn) mn->warm_alpha = nullptr;  // the adjoint's sweeps overwrite the closure state
     if (!mn || !u0 || !alpha0 || !sigma_a || !sigma_s || !q || !block_of_cell || !target || !J ||
         !dJ_dsa || !dJ_dss || nblocks < 1 || nsteps < 0 || ckpt_every < 1 || mn->p.mode != KITRT_FP64)
         return KITRT_EINVAL;
@@ -196,29 +197,50 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
     if (dt <= 0.0) dt = mn->p.cfl * mn->mesh->min_inradius;
     const size_t Cn = (size_t)C * n;
     const int nck = (nsteps + ckpt_every - 1) / ckpt_every;
-    std::vector<void *> owned;
-    auto alloc = [&](size_t bytes) -> void * {
-        void *p = nullptr;
-        if (cudaMalloc(&p, bytes > 0 ? bytes : 1) != cudaSuccess) return nullptr;
-        owned.push_back(p);
-        return p;
-    };
-    auto cleanup = [&](int rc) {
-        for (void *p : owned) cudaFree(p);
-        return rc;
-    };
-    double *ck_u = (double *)alloc(sizeof(double) * Cn * (nck > 0 ? nck : 1));
-    double *ck_a = (double *)alloc(sizeof(double) * Cn * (nck > 0 ? nck : 1));
-    double *seg_u = (double *)alloc(sizeof(double) * Cn * ckpt_every);
-    double *seg_a = (double *)alloc(sizeof(double) * Cn * ckpt_every);
-    double *u = (double *)alloc(sizeof(double) * Cn);
-    double *a = (double *)alloc(sizeof(double) * Cn);
-    double *lam = (double *)alloc(sizeof(double) * Cn);
-    double *lam2 = (double *)alloc(sizeof(double) * Cn);
-    double *Lq = (double *)alloc(sizeof(double) * (size_t)C * Qp);
-    int32_t *fail = (int32_t *)alloc(sizeof(int32_t));
-    for (void *p : owned)
-        if (!p) return cleanup(KITRT_ENOMEM);
+    // the adjoint's buffers live in the solver's workspace: allocated by the first call that
+    // needs them (or needs more than the last), kept for later calls, freed by kitrt_mn_destroy
+    const size_t a256 = 255;
+    const size_t sizes[] = {sizeof(double) * Cn * (nck > 0 ? nck : 1),  // ck_u
+                            sizeof(double) * Cn * (nck > 0 ? nck : 1),  // ck_a
+                            sizeof(double) * Cn * ckpt_every,           // seg_u
+                            sizeof(double) * Cn * ckpt_every,           // seg_a
+                            sizeof(double) * Cn, sizeof(double) * Cn,   // u, a
+                            sizeof(double) * Cn, sizeof(double) * Cn,   // lam, lam2
+                            sizeof(double) * (size_t)C * Qp,            // Lq
+                            sizeof(double) * (1 + 2 * (size_t)nblocks), // J, dJ_dsa, dJ_dss
+                            sizeof(int32_t)};                           // fail
+    constexpr int kBufs = sizeof(sizes) / sizeof(sizes[0]);
+    size_t offs[kBufs], total = 0;
+    for (int i = 0; i < kBufs; ++i) {
+        offs[i] = total;
+        total += (sizes[i] + a256) & ~a256;
+    }
+    if (mn->adj_bytes < total) {
+        if (mn->d_adj) cudaFree(mn->d_adj);
+        mn->d_adj = nullptr;
+        mn->adj_bytes = 0;
+        if (cudaMalloc(&mn->d_adj, total) != cudaSuccess) {
+            mn->d_adj = nullptr;
+            return KITRT_ENOMEM;
+        }
+        mn->adj_bytes = total;
+    }
+    unsigned char *base = (unsigned char *)mn->d_adj;
+    double *ck_u = (double *)(base + offs[0]);
+    double *ck_a = (double *)(base + offs[1]);
+    double *seg_u = (double *)(base + offs[2]);
+    double *seg_a = (double *)(base + offs[3]);
+    double *u = (double *)(base + offs[4]);
+    double *a = (double *)(base + offs[5]);
+    double *lam = (double *)(base + offs[6]);
+    double *lam2 = (double *)(base + offs[7]);
+    double *Lq = (double *)(base + offs[8]);
+    double *dJ = (double *)(base + offs[9]);  // J, then dJ/dsigma_a, then dJ/dsigma_s
+    double *dJ_sa = dJ + 1, *dJ_ss = dJ + 1 + nblocks;
+    int32_t *fail = (int32_t *)(base + offs[10]);
+    auto cleanup = [](int rc) { return rc; };
+    int rc0 = check_stability(mn, sigma_a, sigma_s, dt, s, true);
+    if (rc0) return rc0;
     const Tables T = mn->tables();
     const kitrt_mesh *m = mn->mesh;
     const double inv_m0 = 1.0 / T.m0;
@@ -228,9 +250,7 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
     do {                                               \
         if ((x) != cudaSuccess) return cleanup(KITRT_ECUDA); \
     } while (0)
-    CK(cudaMemsetAsync(J, 0, sizeof(double), s));
-    CK(cudaMemsetAsync(dJ_dsa, 0, sizeof(double) * nblocks, s));
-    CK(cudaMemsetAsync(dJ_dss, 0, sizeof(double) * nblocks, s));
+    CK(cudaMemsetAsync(dJ, 0, sizeof(double) * (1 + 2 * (size_t)nblocks), s));
     CK(cudaMemsetAsync(fail, 0, sizeof(int32_t), s));
     CK(cudaMemcpyAsync(u, u0, sizeof(double) * Cn, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(a, alpha0, sizeof(double) * Cn, cudaMemcpyDeviceToDevice, s));
@@ -242,7 +262,7 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
         }
         {
             LaunchScope ls(mn, PK_ADJOINT, s, C);
-            objective_kernel<<<tb, 256, 0, s>>>(u, n, sigma_a, target, m->d_area, dt, inv_m0, C, J);
+            objective_kernel<<<tb, 256, 0, s>>>(u, n, sigma_a, target, m->d_area, dt, inv_m0, C, dJ);
         }
         const int rc = kitrt_internal_step(mn, u, a, sigma_a, sigma_s, q, dt, st == 0, s);
         if (rc) return cleanup(rc);
@@ -268,8 +288,8 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
         adjoint_cell_kernel<NNv><<<wb, kWarps * 32, 0, s>>>(T, m->d_nbr, m->d_nrm, m->d_area,               \
                                                             seg_u + Cn * (st - s0), seg_a + Cn * (st - s0), \
                                                             lam, Lq, sigma_a, sigma_s, target,              \
-                                                            block_of_cell, dt, mn->p.bc, C, lam2, dJ_dsa,   \
-                                                            dJ_dss, fail);                                  \
+                                                            block_of_cell, dt, mn->p.bc, C, lam2, dJ_sa,    \
+                                                            dJ_ss, fail);                                   \
         break;
             switch (mn->N) {
                 ADJ_CASE(1)
@@ -288,6 +308,9 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
     }
     int32_t nf = 0;
     CK(cudaMemcpyAsync(&nf, fail, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(J, dJ, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(dJ_dsa, dJ_sa, sizeof(double) * nblocks, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(dJ_dss, dJ_ss, sizeof(double) * nblocks, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
 #undef CK
     return cleanup(nf ? KITRT_ECHOL : KITRT_OK);

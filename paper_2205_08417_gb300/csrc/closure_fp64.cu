@@ -24,12 +24,17 @@ constexpr int kWarps = 8;  // warps per block
 constexpr int kThreadBlock = 64;  // block of the thread-per-cell Newton kernels
 
 // ---------------------------------------------------------------------------------------------
-// begin: start a closure. first != 0: every cell starts from alpha_in with an evaluation.
+// begin: start a closure. first == 1: every cell starts from alpha_in with an evaluation.
 // first == 0: the previous closure left alpha_k, its moments U, <exp>, and the Cholesky factor
 // of H(alpha_k); with the new u the gradient is U - u. One thread per cell tests it: a cell
 // already converged (and with no polish step to take) is done at once; the others go to the
 // predictor list, where predict_kernel takes the first Newton direction from the stored factor
 // without a new quadrature pass.
+// first == 2: per cell, the second case when alpha_in is bit for bit the alpha the last closure
+// returned for this cell (alpha_k, plus the polish step when polishing) and that closure
+// succeeded, so the stored state is exactly the state behind the given alpha; the first case
+// otherwise (the cell's stored <exp> is then poisoned, so that the learned pass cannot mistake
+// it for a previous point).
 // ---------------------------------------------------------------------------------------------
 
 // Warp-aggregated append of `cell` to a list when pred holds (all active lanes call it).
@@ -54,6 +59,18 @@ begin_test_kernel(NewtonState S, const double *__restrict__ u, const double *__r
     constexpr int n = Dims<NN>::n;
     for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < C; cell += gridDim.x * blockDim.x) {
         const size_t off = (size_t)cell * n;
+        bool cold = first == 1;
+        if (first == 2) {
+            // the alpha the finish kernel returned: alpha_k (+ the polish step when polishing)
+            bool same = S.status[cell] == 0;
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                double out = S.alpha[off + a];
+                if (np.polish) out += S.dir[off + a];
+                same = same && __double_as_longlong(out) == __double_as_longlong(alpha_in[off + a]);
+            }
+            cold = !same;
+        }
         S.iters[cell] = 0;
         S.halv[cell] = 0;
         S.evals[cell] = 0;
@@ -61,10 +78,11 @@ begin_test_kernel(NewtonState S, const double *__restrict__ u, const double *__r
         if (S.h64) S.h64[cell] = 0;
         if (S.gnorm) S.gnorm[cell] = INFINITY;
         bool to_eval = false, to_predict = false;
-        if (first) {
+        if (cold) {
 #pragma unroll
             for (int a = 0; a < n; ++a) S.alpha[off + a] = alpha_in[off + a];
             S.phase[cell] = PH_INIT;
+            if (first == 2) S.fsum[cell] = __longlong_as_double(0x7ff8000000000000LL);
             // learned closures go to the network first (the predictor list doubles as its list)
             to_eval = !learned;
             to_predict = learned;
@@ -483,7 +501,7 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
         KITRT_DISPATCH_N(mn->N, begin_test_kernel<NN><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(S, u, alpha_in, first, np, C, learned));
         if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
     }
-    if (first || learned) return KITRT_OK;
+    if (first == 1 || learned) return KITRT_OK;
     LaunchScope ls(mn, PK_BEGIN, s, 0);
     KITRT_DISPATCH_N(mn->N, predict_launch<NN>(mn, S, C, u, np, s));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;

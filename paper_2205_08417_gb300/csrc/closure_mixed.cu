@@ -410,13 +410,7 @@ int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const
                       float *psi32)
 {
     using L = MixedSmem<NN, BF16>;
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(eval_mixed_kernel<NN, BF16, MO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 L::total) != cudaSuccess)
-            return KITRT_ECUDA;
-        configured = true;
-    }
+    if (ensure_dyn_smem(eval_mixed_kernel<NN, BF16, MO>, L::total)) return KITRT_ECUDA;
     // persistent grid of one CTA per SM; aim at two work items per CTA
     const int tiles = (C + kTileM - 1) / kTileM;
     const int grid = tiles < mn->nsm ? (tiles > 0 ? tiles : 1) : mn->nsm;

@@ -1,17 +1,17 @@
 // Allocation-free variant of the entropy closure (kitrt_closure_noalloc).
 //
 // Some callers cannot let the library allocate device memory when they call it: code that runs
-// while its framework's pool allocator owns all free device memory, code inside a region where
-// cudaMalloc is not allowed (for instance while a stream is being captured), or a long-running
-// service that must not grow its footprint after start-up. kitrt_closure needs the solver's
-// mesh-sized workspace; this entry point instead solves the closure of any batch of up to a fixed
-// number of moment vectors with its Newton scratch in one file-scope device array, so a call
-// allocates nothing.
+// while its framework's pool allocator owns all free device memory (a cudaMalloc there fails or
+// makes the pool give memory back), or a long-running service that must not grow its footprint
+// after start-up. kitrt_closure needs the solver's mesh-sized workspace; this entry point instead
+// solves the closure of any batch of up to a fixed number of moment vectors with its Newton
+// scratch in one file-scope device array, so a call allocates nothing.
 //
 // The scratch array is kScratchBytes (8 MiB) per GPU that loads the library and stays resident
 // until the process exits. Every call shares it and it keeps the last call's contents; the call
 // clears the counters that must start at zero and every per-cell field is written before it is
-// read. Calls that overlap on the GPU (two streams, or two host threads) race on the array.
+// read. Calls that overlap on the GPU (two streams, or two host threads) race on the array. The
+// host reads the counters back (and synchronises with the stream) once every four sweeps.
 #include <mutex>
 #include <string.h>
 

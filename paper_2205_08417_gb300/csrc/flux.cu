@@ -10,6 +10,8 @@
 // uniform state gives exactly zero flux at any working precision. F is projected on the basis,
 // warp-reduced, and u <- u - dt/A F + dt R(u) is applied in place (the flux reads psi only).
 // psi rows are contiguous per cell, so each face gather is a coalesced row segment.
+#include <string.h>
+
 #include "kitrt_internal.cuh"
 
 namespace {
@@ -251,4 +253,73 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
     }
 #undef FLUX_CASE
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
+}
+
+// Stability of the explicit step. The first-order kinetic update of the ansatz at quadrature
+// point q keeps psi_iq (1 - dt/A_i sum_f (Omega_q.n_f)^+ - dt sigma_t,i) of the cell's own value;
+// for a triangle sum_f (Omega.n_f)^+ = 1/2 sum_f |Omega.n_f| <= P_i / 2, so
+//     dt (P_i / (2 A_i) + sigma_a,i + sigma_s,i) <= 1
+// in every cell keeps every updated ordinate a non-negative combination of non-negative values
+// (scattering and source only add), and the updated moments realizable. This is the cell-wise
+// form of dt sigma_t,max <= 1 - CFL with CFL = dt / min_i (2 A_i / P_i), which implies it.
+namespace {
+
+__global__ void stability_kernel(const double *__restrict__ hpa, const double *__restrict__ sa,
+                                 const double *__restrict__ ss, double dt, int C,
+                                 unsigned long long *__restrict__ out)
+{
+    double worst = 0.0;
+    unsigned bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
+        const double a = sa[i], b = ss[i];
+        if (!(a >= 0.0) || !(b >= 0.0) || !isfinite(a) || !isfinite(b)) ++bad;
+        else worst = fmax(worst, dt * (hpa[i] + a + b));
+    }
+    // non-negative doubles order like their bit patterns
+    unsigned long long wb = __double_as_longlong(worst);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xffffffffu, wb, o);
+        wb = x > wb ? x : wb;
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], wb);
+        if (bad) atomicAdd(&out[1], (unsigned long long)bad);
+    }
+}
+
+}  // namespace
+
+int check_stability(kitrt_mn *mn, const double *sa, const double *ss, double dt, cudaStream_t s,
+                    bool wait)
+{
+    const int C = mn->mesh->C;
+    if (!(dt > 0.0) || !isfinite(dt)) return KITRT_EINVAL;
+    if (cudaMemsetAsync(mn->d_check, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
+        return KITRT_ECUDA;
+    int blocks = (C + 255) / 256;
+    if (blocks > mn->nsm * 4) blocks = mn->nsm * 4;
+    {
+        LaunchScope ls(mn, PK_OTHER, s, C);
+        stability_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(mn->mesh->d_hpa, sa, ss, dt, C,
+                                                                  mn->d_check);
+    }
+    if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
+    if (cudaMemcpyAsync(mn->h_check, mn->d_check, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return KITRT_ECUDA;
+    if (!wait) return KITRT_OK;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return KITRT_ECUDA;
+    return stability_verdict(mn);
+}
+
+// Reads the test's result (the stream must have passed the copy in check_stability).
+int stability_verdict(const kitrt_mn *mn)
+{
+    if (mn->h_check[1] != 0) return KITRT_EINVAL;
+    double worst;
+    memcpy(&worst, &mn->h_check[0], sizeof(double));
+    // a relative slack of 1e-12 keeps dt = 1 / max(...) itself admissible after rounding
+    return worst <= 1.0 + 1e-12 ? KITRT_OK : KITRT_EINVAL;
 }

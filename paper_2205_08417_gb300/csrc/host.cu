@@ -302,9 +302,13 @@ int32_t kitrt_mesh_create(const double *xy, int32_t nverts, const int32_t *tri, 
     std::vector<int4> nb4(ntri);
     for (int32_t c = 0; c < ntri; ++c)
         nb4[c] = make_int4(m->nbr[3 * c], m->nbr[3 * c + 1], m->nbr[3 * c + 2], 0);
+    std::vector<double> hpa(ntri);
+    for (int32_t c = 0; c < ntri; ++c) hpa[c] = m->perim[c] / (2.0 * m->area[c]);
     bool ok = cudaMalloc(&m->d_nbr, sizeof(int4) * ntri) == cudaSuccess &&
               cudaMalloc(&m->d_nrm, sizeof(double) * 6 * ntri) == cudaSuccess &&
-              cudaMalloc(&m->d_area, sizeof(double) * ntri) == cudaSuccess;
+              cudaMalloc(&m->d_area, sizeof(double) * ntri) == cudaSuccess &&
+              cudaMalloc(&m->d_hpa, sizeof(double) * ntri) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_hpa, hpa.data(), sizeof(double) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_nbr, nb4.data(), sizeof(int4) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_nrm, m->nrm.data(), sizeof(double) * 6 * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_area, m->area.data(), sizeof(double) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -322,6 +326,7 @@ int32_t kitrt_mesh_destroy(kitrt_mesh *m)
     cudaFree(m->d_nbr);
     cudaFree(m->d_nrm);
     cudaFree(m->d_area);
+    cudaFree(m->d_hpa);
     delete m;
     return KITRT_OK;
 }
@@ -352,6 +357,8 @@ int32_t kitrt_mn_destroy(kitrt_mn *mn)
     for (void *p : mn->allocs) cudaFree(p);
     if (mn->h_cnt) cudaFreeHost(mn->h_cnt);
     if (mn->h_sn_flag) cudaFreeHost(mn->h_sn_flag);
+    if (mn->h_check) cudaFreeHost(mn->h_check);
+    if (mn->d_adj) cudaFree(mn->d_adj);
     delete mn;
     return KITRT_OK;
 }
@@ -521,6 +528,14 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_alloc(mn, &S.list[0], C));
     TRY(dev_alloc(mn, &S.list[1], C));
     TRY(dev_alloc(mn, &S.cnt, 16));
+    // no cell has a closure state yet: NaN alphas never equal a caller's alpha bit for bit, so the
+    // first kitrt_step starts every cell from its given alpha
+    if (cudaMemset(S.alpha, 0xff, sizeof(double) * C * n) != cudaSuccess ||
+        cudaMemset(S.dir, 0, sizeof(double) * C * n) != cudaSuccess ||
+        cudaMemset(S.status, 0xff, sizeof(int32_t) * C) != cudaSuccess) {
+        kitrt_mn_destroy(mn);
+        return KITRT_ECUDA;
+    }
     TRY(dev_alloc(mn, &mn->d_psi, C * Qp));
     TRY(dev_alloc(mn, &mn->d_Vacc, C * (size_t)n2));
     if (cudaMemset(mn->d_Vacc, 0, sizeof(double) * C * (size_t)n2) != cudaSuccess) {
@@ -549,6 +564,11 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
         double *cellc = nullptr;
         TRY(dev_alloc(mn, &cellc, C * 12));
         mn->d_sn_cell = cellc;
+    }
+    TRY(dev_alloc(mn, &mn->d_check, 2));
+    if (cudaMallocHost(&mn->h_check, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        kitrt_mn_destroy(mn);
+        return KITRT_ENOMEM;
     }
     if (cudaMallocHost(&mn->h_sn_flag, sizeof(int32_t)) != cudaSuccess) {
         kitrt_mn_destroy(mn);
@@ -635,7 +655,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
     if (rc) return rc;
     if (learned) {
         rc = launch_mlp_infer(mn, u, mn->st.list[1], mn->st.cnt + 8, C, mn->d_alpha_nn, s);
-        if (!rc) rc = launch_learned_pass(mn, T, mn->st, C, u, psi32, first, s);
+        if (!rc) rc = launch_learned_pass(mn, T, mn->st, C, u, psi32, first == 1, s);
         if (rc) return rc;
     }
     const int batch = 4;
@@ -657,7 +677,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
             if (!rc) rc = launch_post(mn, T, mn->st, C, u, k, np, mn->d_Vacc, s);
             if (rc) return rc;
         }
-        CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 10 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CUDA_OK(cudaStreamSynchronize(s));
         if (mn->h_cnt[7]) return mn->h_cnt[7];
         int active = mn->h_cnt[k % 3];
@@ -671,6 +691,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
         stats->max_evals = std::max(stats->max_evals, mn->h_cnt[4]);
         stats->failed = mn->h_cnt[3];
         stats->fallbacks += mn->h_cnt[5];
+        stats->restarts += mn->h_cnt[9];
     }
     if (mn->h_cnt[3] > 0) {
         // report the first failing code
@@ -710,13 +731,9 @@ int32_t kitrt_closure_batch(kitrt_mn *mn, const double *u, double *alpha, int32_
     cudaStream_t s = (cudaStream_t)stream;
     if (stats) memset(stats, 0, sizeof(*stats));
     const int64_t launches0 = mn->launch_count;
-    mn->warm_alpha = nullptr;
     int rc = run_closure(mn, ncells, u, alpha, 1, s, stats);
     int rc2 = launch_finish(mn, mn->tables(), mn->st, ncells, alpha, nullptr, nullptr,
                             polish_of(mn), 0, s);
-    // a full-mesh closure leaves a state a following kitrt_step can continue from (a partial
-    // batch leaves the other cells' ansatz out of date)
-    if (!rc && !rc2 && ncells == mn->mesh->C && mn->p.mode == KITRT_FP64) mn->warm_alpha = alpha;
     if (status)
         CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * ncells,
                                 cudaMemcpyDeviceToDevice, s));
@@ -755,17 +772,27 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
     const int C = mn->mesh->C;
     const Tables T = mn->tables();
     if (nsteps == 0) return KITRT_OK;
-    // the same alpha buffer as the last successful full-mesh closure: continue from the solver's
-    // own state (the Newton predictor starts from the stored factor); else start from alpha
-    const bool cont = mn->warm_alpha == alpha;
-    mn->warm_alpha = nullptr;
-    int rc = KITRT_OK;
+    // first step: each cell whose given alpha is, bit for bit, the one the solver last returned
+    // for it continues from the stored state of that closure (the Newton predictor starts from
+    // the stored factor), every other cell from its given alpha; after kitrt_mn_reset every cell
+    // starts from its given alpha. Later steps continue from the previous step's closure.
+    const int first = mn->force_cold ? 1 : 2;
+    mn->force_cold = false;
+    // stability of the explicit step (positivity of the kinetic update at every quadrature point):
+    // dt (P_i / (2 A_i) + sigma_a,i + sigma_s,i) <= 1 in every cell; the test's result is read
+    // back with the first closure's completion counters, before u is touched
+    int rc = check_stability(mn, sigma_a, sigma_s, dt, s, false);
+    if (rc) return rc;
     for (int32_t it = 0; it < nsteps; ++it) {
         const bool fp64 = mn->p.mode == KITRT_FP64;
         // mixed modes: the evaluation sweeps write the FP32 ansatz of every accepted point, and
         // with no polish step the solution's ansatz is already in place
-        rc = run_closure(mn, C, u, alpha, it == 0 && !cont, s, stats, fp64 ? nullptr : mn->d_psi32);
+        rc = run_closure(mn, C, u, alpha, it == 0 ? first : 0, s, stats, fp64 ? nullptr : mn->d_psi32);
+        if (!rc && it == 0) rc = stability_verdict(mn);
         if (rc) break;
+        // compare_prev (skip psi when alpha is bitwise unchanged) only once alpha holds the
+        // previous step's output, which is always the case after the first step of a call and for
+        // a first step that continued every cell; a cold first step recomputes psi everywhere
         rc = launch_finish(mn, T, mn->st, C, alpha, fp64 ? mn->d_psi : nullptr, nullptr,
                            polish_of(mn), it > 0, s);
         if (rc) break;
@@ -773,7 +800,6 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
                                 u, sigma_a, sigma_s, q, dt, mn->p.bc, s);
         if (rc) break;
     }
-    if (!rc) mn->warm_alpha = alpha;
     if (status)
         CUDA_OK(cudaMemcpyAsync(status, mn->st.status, sizeof(int32_t) * C,
                                 cudaMemcpyDeviceToDevice, s));
@@ -787,7 +813,7 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
 int32_t kitrt_mn_reset(kitrt_mn *mn)
 {
     if (!mn) return KITRT_EINVAL;
-    mn->warm_alpha = nullptr;
+    mn->force_cold = true;
     return KITRT_OK;
 }
 

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "kitrt.h"
@@ -24,6 +27,7 @@ struct kitrt_mesh {
     int4 *d_nbr = nullptr;     // [C] neighbours across faces 0..2 (-1 = boundary), .w unused
     double *d_nrm = nullptr;   // [C x 6] scaled outward normals (nx0, ny0, nx1, ny1, nx2, ny2)
     double *d_area = nullptr;  // [C]
+    double *d_hpa = nullptr;   // [C] P_i / (2 A_i): largest outflow rate of the cell per unit speed
 };
 
 // Device views handed to kernels by value.
@@ -63,7 +67,8 @@ struct NewtonState {
     int32_t *list[2];  // active cell lists (ping-pong)
     int32_t *cnt;      // [16]: cnt[0..2] rotating list counters, cnt[3] failures, cnt[4] max
                        //   evals, cnt[5] fallbacks, cnt[6] evaluations, cnt[7] timeout status,
-                       //   cnt[8] predictor list length
+                       //   cnt[8] predictor list length, cnt[9] learned-mode steps taken
+                       //   from a stored factor
 };
 
 struct NewtonParams {
@@ -110,9 +115,14 @@ struct kitrt_mn {
     double *d_psi = nullptr;   // [C x Qp] FP64 ansatz
     float *d_psi32 = nullptr;  // [C x Qp] FP32 ansatz (mixed modes)
     int32_t *h_cnt = nullptr;  // pinned copy of st.cnt
-    // alpha buffer of the last successful full-mesh closure (kitrt_step, kitrt_closure): a
-    // kitrt_step given the same buffer continues from the solver's state (warm predictor)
-    const double *warm_alpha = nullptr;
+    // kitrt_mn_reset: the next kitrt_step starts every cell from its given alpha (otherwise each
+    // cell whose given alpha is the one the solver last returned continues from its stored state)
+    bool force_cold = false;
+    // stability test of kitrt_step / kitrt_adjoint: [0] largest dt (P/2A + sigma_a + sigma_s) as
+    // the bits of a non-negative double, [1] cells with a negative or non-finite coefficient
+    unsigned long long *d_check = nullptr, *h_check = nullptr;
+    void *d_adj = nullptr;     // kitrt_adjoint workspace (grown on demand)
+    size_t adj_bytes = 0;
     int32_t *d_sn_flag = nullptr;  // S_N step: device status (KITRT_ETIMEOUT on an expired wait)
     int32_t *h_sn_flag = nullptr;  // pinned copy
     void *d_sn_cell = nullptr;     // [C x 12] per-cell coefficients of the S_N step (FP32 or FP64)
@@ -135,6 +145,25 @@ struct LaunchScope {
     LaunchScope(kitrt_mn *m, int k, cudaStream_t st, int64_t units);
     ~LaunchScope();
 };
+
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on the current device.
+// The attribute is per device, so the record is keyed by (kernel, device).
+template <typename Kern>
+inline int ensure_dyn_smem(Kern *kernel, size_t smem)
+{
+    static std::mutex mtx;
+    static std::map<std::pair<const void *, int>, size_t> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return KITRT_ECUDA;
+    std::lock_guard<std::mutex> lock(mtx);
+    size_t &have = done[std::make_pair((const void *)kernel, dev)];
+    if (have >= smem) return KITRT_OK;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return KITRT_ECUDA;
+    have = smem;
+    return KITRT_OK;
+}
 
 // Kernel launchers (closure_fp64.cu, flux.cu).
 int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cudaStream_t s);
@@ -161,6 +190,9 @@ int launch_eval_mixed(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C
                       int k, NewtonParams np, cudaStream_t s, float *psi32);
 int launch_moments_mixed(kitrt_mn *mn, const Tables &T, int C, const double *alpha, double *Vout,
                          cudaStream_t s);
+int check_stability(kitrt_mn *mn, const double *sa, const double *ss, double dt, cudaStream_t s,
+                    bool wait);
+int stability_verdict(const kitrt_mn *mn);
 int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
                        const float *psi32, double *u, const double *sa, const double *ss,
                        const double *q, double dt, int bc, cudaStream_t s);

@@ -86,7 +86,7 @@ learned_pass_kernel(Tables T, NewtonState S, const double *__restrict__ u,
             // Newton starts from the better of the network's point and the cell's previous alpha
             // (its objective needs no quadrature: <exp> of the previous point is stored)
             bool use_nn = finite;
-            if (!first && finite) {
+            if (first != 1 && finite) {
                 const double ap = lane < n ? S.alpha[off + lane] : 0.0;
                 const double f_prev = S.fsum[cell] - warp_sum(ap * ua);
                 use_nn = !(isfinite(f_prev) && f_prev <= f_nn);
@@ -95,7 +95,7 @@ learned_pass_kernel(Tables T, NewtonState S, const double *__restrict__ u,
                 if (lane == 0) S.alpha[off] = alpha0;
                 if (lane >= 1 && lane < n) S.alpha[off + lane] = al;
             }
-            if (!use_nn && !first && S.lfac && S.lfac[cell]) {
+            if (!use_nn && first != 1 && S.lfac && S.lfac[cell]) {
                 // the previous closure's point is the better start, and its moments and a
                 // factor of this cell are stored: take the Newton step from them at once, as the
                 // predictor of the other modes does, instead of evaluating that point again
@@ -116,6 +116,7 @@ learned_pass_kernel(Tables T, NewtonState S, const double *__restrict__ u,
                     S.lam[cell] = 1.0;
                     S.phase[cell] = PH_NEWTON;
                     atomicAdd(&S.cnt[5], 1);
+                    atomicAdd(&S.cnt[9], 1);  // a step from the stored factor
                 }
             } else if (lane == 0) {
                 S.phase[cell] = PH_INIT;

@@ -350,9 +350,7 @@ int launch_mlp_infer(kitrt_mn *mn, const double *u, const int32_t *list, const i
     LaunchScope ls(mn, PK_MLP, s, C);
 #define INFER_CASE(D)                                                                                        \
     case D:                                                                                                  \
-        if (cudaFuncSetAttribute(mlp_infer_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != \
-            cudaSuccess)                                                                                     \
-            return KITRT_ECUDA;                                                                              \
+        if (ensure_dyn_smem(mlp_infer_kernel<D>, smem)) return KITRT_ECUDA;                                 \
         mlp_infer_kernel<D><<<blocks, 128, smem, s>>>((const __nv_bfloat16 *)mn->d_mlp16, mn->d_mlp_norm, u, list, \
                                                       cnt, C, alpha);                                        \
         break;

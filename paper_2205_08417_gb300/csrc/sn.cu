@@ -350,13 +350,7 @@ int launch_sn_v(kitrt_mn *mn, const SnTab<P> &T, const P *psi, P *out, const P *
     TC = TC < 4 ? 4 : (TC > 32 ? 32 : TC & ~3);
     const size_t buf_bytes = ((size_t)TC * T.Qf * sizeof(P) + 127) / 128 * 128;
     const size_t smem = kHeader + 2 * buf_bytes + (size_t)TC * nm * sizeof(P);
-    static size_t configured = 0;
-    if (smem > configured) {
-        if (cudaFuncSetAttribute(sn_tile_kernel<P, NN, ISO, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return KITRT_ECUDA;
-        configured = smem;
-    }
+    if (ensure_dyn_smem(sn_tile_kernel<P, NN, ISO, V>, smem)) return KITRT_ECUDA;
     int resident = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sn_tile_kernel<P, NN, ISO, V>, kThreads,
                                                       smem) != cudaSuccess ||

@@ -37,7 +37,7 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("closures", C.c_int64), ("evaluations", C.c_int64), ("max_evals", C.c_int32),
                 ("failed", C.c_int32), ("fallbacks", C.c_int64), ("dt", C.c_double),
-                ("launches", C.c_int64)]
+                ("launches", C.c_int64), ("restarts", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -262,17 +262,18 @@ class MNSolver:
 
     def adjoint(self, u0, alpha0, sigma_a, sigma_s, q, block_of_cell, nblocks, target, dt, nsteps,
                 ckpt_every=16):
-        """(J, dJ/dsigma_a per block, dJ/dsigma_s per block) as device FP64 tensors."""
+        """(J, dJ/dsigma_a per block, dJ/dsigma_s per block): a float and two host FP64 arrays."""
         import torch
-        J = torch.empty(1, dtype=torch.float64, device=u0.device)
-        gsa = torch.empty(nblocks, dtype=torch.float64, device=u0.device)
-        gss = torch.empty(nblocks, dtype=torch.float64, device=u0.device)
+        J = np.zeros(1)
+        gsa = np.zeros(int(nblocks))
+        gss = np.zeros(int(nblocks))
         _check(_lib().kitrt_adjoint(self.handle, _dev(u0, torch.float64), _dev(alpha0, torch.float64),
                                     _dev(sigma_a, torch.float64), _dev(sigma_s, torch.float64),
                                     _dev(q, torch.float64), _dev(block_of_cell, torch.int32), int(nblocks),
                                     _dev(target, torch.uint8), float(dt), int(nsteps), int(ckpt_every),
-                                    _dev(J), _dev(gsa), _dev(gss), _stream()), "kitrt_adjoint")
-        return J, gsa, gss
+                                    J.ctypes.data_as(C.c_void_p), gsa.ctypes.data_as(C.c_void_p),
+                                    gss.ctypes.data_as(C.c_void_p), _stream()), "kitrt_adjoint")
+        return float(J[0]), gsa, gss
 
     def set_mlp(self, params, norm, hidden: int = 64):
         import torch

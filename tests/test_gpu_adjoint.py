@@ -47,7 +47,7 @@ def gpu_J_grad(K, s, blk, sa, ss, q, tgt, u0, dt, nsteps, ckpt):
     ad = s.isotropic_alpha(ud)
     J, gsa, gss = s.adjoint(ud, ad, dev(sa[blk]), dev(ss[blk]), dev(q), dev(blk.astype(np.int32)),
                             len(sa), dev(tgt), dt, nsteps, ckpt)
-    return float(J.cpu()[0]), gsa.cpu().numpy(), gss.cpu().numpy()
+    return J, gsa, gss
 
 
 @pytest.mark.parametrize("ckpt", [5, 16])

@@ -331,3 +331,79 @@ def test_step_calls_continue_from_the_solver_state(K):
     s.reset()
     s.step(ud, ad, sa, ss, q, dt=dt, nsteps=1)  # cold, from the same alpha
     assert (torch.linalg.norm(uc - ud) / torch.linalg.norm(uc)).item() <= 1e-12
+
+
+def test_a_new_warm_start_in_a_reused_buffer_starts_cold(K):
+    """Continuation is decided per cell by the alpha's contents, not by the buffer it sits in: a
+    warm start written into the buffer of the last call, or into a freshly allocated buffer that
+    may reuse a freed one's address, gives bitwise the result of a solver that never stepped
+    (a cold start); the solver's own output passed back in a different buffer continues."""
+    m = synth.jittered_mesh(45, -1.5, 1.5, seed=1)
+    mesh = K.Mesh(m.xy, m.tri)
+    C = mesh.ncells
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sa, ss, q = dev(np.zeros(C)), dev(np.ones(C)), dev(np.zeros(C))
+    dt = 0.4 * mesh.geometry()["min_inradius"]
+    s = K.MNSolver(mesh, 2, 10, tau=1e-10)
+    u0 = synth.isotropic_moments(synth.line_source_density(m.centroids()), s.n)
+    ua = dev(u0)
+    aa = s.isotropic_alpha(ua)
+    s.step(ua, aa, sa, ss, q, dt=dt, nsteps=5)
+    u_mid = ua.clone()
+    # (1) a new warm start written into the same buffer (every row differs from the solver's
+    # output: its alpha_0 is scaled)
+    aa.copy_(aa * 0.999)
+    a_start = aa.clone()
+    _, st = s.step(ua, aa, sa, ss, q, dt=dt, nsteps=3, stats=True)
+    fresh = K.MNSolver(mesh, 2, 10, tau=1e-10)
+    ub = u_mid.clone()
+    ab = a_start
+    _, st_fresh = fresh.step(ub, ab, sa, ss, q, dt=dt, nsteps=3, stats=True)
+    assert torch.equal(ua, ub) and torch.equal(aa, ab)
+    assert st["evaluations"] == st_fresh["evaluations"]
+    # (2) the old buffer freed, a new one allocated (the caching allocator may hand back the same
+    # address) and filled with a different warm start
+    ptr = aa.data_ptr()
+    u_mid2 = ua.clone()
+    del aa
+    torch.cuda.synchronize()
+    ac = torch.empty((C, s.n), dtype=torch.float64, device="cuda")
+    ac.copy_(s.isotropic_alpha(ua) * 1.001)
+    print("reallocated at the same address:", ac.data_ptr() == ptr)
+    s.step(ua, ac, sa, ss, q, dt=dt, nsteps=2)
+    fresh2 = K.MNSolver(mesh, 2, 10, tau=1e-10)
+    ud = u_mid2.clone()
+    ad = fresh2.isotropic_alpha(ud) * 1.001
+    fresh2.step(ud, ad, sa, ss, q, dt=dt, nsteps=2)
+    assert torch.equal(ua, ud) and torch.equal(ac, ad)
+    # (3) the solver's own output, copied to another buffer, continues: fewer passes than cold
+    ae = ac.clone()
+    _, st_cont = s.step(ua, ae, sa, ss, q, dt=dt, nsteps=1, stats=True)
+    assert st_cont["evaluations"] < C
+
+
+def test_step_rejects_an_unstable_time_step_before_touching_u(K):
+    """dt (P_i/(2 A_i) + sigma_a,i + sigma_s,i) <= 1 in every cell keeps the kinetic update of every
+    ordinate positive; a step beyond it, or a negative coefficient, returns EINVAL and leaves u
+    and alpha as they were."""
+    m = synth.jittered_mesh(20, 0.0, 1.0, seed=3)
+    mesh = K.Mesh(m.xy, m.tri)
+    C = mesh.ncells
+    g = mesh.geometry()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s = K.MNSolver(mesh, 2, 10, tau=1e-10)
+    u = dev(synth.isotropic_moments(np.full(C, 1.0), s.n))
+    a = s.isotropic_alpha(u)
+    sa, ss, q = np.zeros(C), np.ones(C), np.zeros(C)
+    hpa = g["perim"] / (2 * g["area"])
+    dt_max = 1.0 / (hpa + sa + ss).max()
+    u_keep, a_keep = u.clone(), a.clone()
+    rc = s.step(u, a, dev(sa), dev(ss), dev(q), dt=1.01 * dt_max, nsteps=2, check=False)
+    assert rc == 1 and torch.equal(u, u_keep) and torch.equal(a, a_keep)
+    bad = ss.copy()
+    bad[C // 2] = -0.5
+    rc = s.step(u, a, dev(sa), dev(bad), dev(q), dt=0.5 * dt_max, nsteps=1, check=False)
+    assert rc == 1 and torch.equal(u, u_keep)
+    # at the bound itself the step runs
+    rc = s.step(u, a, dev(sa), dev(ss), dev(q), dt=dt_max, nsteps=1, check=False)
+    assert rc == 0

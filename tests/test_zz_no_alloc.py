@@ -2,12 +2,12 @@
 kitrt_closure.
 
 kitrt_closure_noalloc exists for callers that cannot let the library allocate device memory at
-call time (a pool allocator owns the free memory, a stream is being captured, a service must not
-grow after start-up). It keeps its Newton state in a fixed static device array that every call
-shares, so this test calls it twice in a row on different batches and checks both answers against
-the ordinary entry point, and checks that an oversized batch is refused before any memory is
-touched. This file is collected last on purpose, and it does not rely on anything the other tests
-leave behind, so it passes alone in a fresh process as well."""
+call time: a framework whose pool allocator already owns the free device memory, or a service
+that must not grow its footprint after start-up. It keeps its Newton state in a fixed static
+device array that every call shares, so this test calls it twice in a row on different batches
+and checks both answers against the ordinary entry point, and checks that an oversized batch is
+refused before any memory is touched. This file is collected last on purpose, and it does not
+rely on anything the other tests leave behind, so it passes alone in a fresh process as well."""
 import math
 
 import numpy as np
