@@ -24,7 +24,9 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
         return _OUT
-    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-D_DEFAULT_SOURCE", _SRC, "-o",
+    # -O3 without -march=native or fast-math: ISO C99 mode contracts no multiply-adds, so the
+    # oracle rounds the same way on the x86-64 and aarch64 hosts it runs on
+    base = ["gcc", "-O3", "-fPIC", "-shared", "-std=c99", "-D_DEFAULT_SOURCE", _SRC, "-o",
             _OUT + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
@@ -71,6 +73,9 @@ def _declare(L):
                               d, i, _dp, _dp, i]
     L.orc_sn_run.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
                              d, i, i, _dp, _dp, i]
+    L.orc_step_vjp.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, d, i, _dp,
+                               _dp, _dp, _dp]
+    L.orc_step_jvp.argtypes = L.orc_step_vjp.argtypes
     L.orc_mlp_forward.argtypes = [i, i, i, i, _dp, _dp, _dp]
     L.orc_mlp_loss_grad.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp]
     L.orc_mlp_loss_grad.restype = d
@@ -248,6 +253,28 @@ def mn_adjoint(T, G, block_of_cell, sa_blk, ss_blk, qsrc, target, dt, nsteps, u0
     if nf:
         raise RuntimeError(f"oracle adjoint: {nf} failed closures")
     return float(J[0]), gsa, gss
+
+
+def step_vjp(T, G, u, alpha, sigma_a, sigma_s, dt, lam, bc=0):
+    """(du^{s+1}/du^s)^T lam at (u, alpha) (alpha = the closure of u)."""
+    out = np.zeros_like(u)
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    nf = lib().orc_step_vjp(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                            _d(G.nrm), _d(G.area), f(sigma_a), f(sigma_s), dt, bc, f(u), f(alpha),
+                            f(lam), _d(out))
+    assert nf == 0
+    return out
+
+
+def step_jvp(T, G, u, alpha, sigma_a, sigma_s, dt, du, bc=0):
+    """(du^{s+1}/du^s) du at (u, alpha), in forward mode."""
+    out = np.zeros_like(u)
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    nf = lib().orc_step_jvp(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                            _d(G.nrm), _d(G.area), f(sigma_a), f(sigma_s), dt, bc, f(u), f(alpha),
+                            f(du), _d(out))
+    assert nf == 0
+    return out
 
 
 def mn_objective(T, G, block_of_cell, sa_blk, ss_blk, qsrc, target, dt, nsteps, u0, alpha0, bc=1,

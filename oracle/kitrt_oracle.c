@@ -18,7 +18,8 @@
  *   - Kinetic upwind flux of the closed ansatz [Sec. 4.4, last flux equation] and the explicit
  *     first-order update [Sec. 4.2, explicit iteration] with isotropic scattering, absorption and
  *     an isotropic source [Sec. 3.1 moment equations: scattering diagonal in moments].
- *   - Discrete adjoint of that step (exact transpose, closure derivative dalpha/du = H^-1).
+ *   - Discrete adjoint of that step (exact transpose, closure derivative dalpha/du = H^-1), and
+ *     the one-step tangent written separately in forward mode (for the transpose test).
  *   - The S_N step of the nodal system [Sec. 2, Eq. SNEqns2] with the P_N form O Sigma M of the
  *     scattering operator and the same upwind flux applied per ordinate.
  *   - Plain MLP (softplus) forward/backward and Adam, for the learned-closure gradient checks.
@@ -26,7 +27,8 @@
  * Quadrature sums here always run over the full, unfolded point set Q; the CUDA path folds the
  * +-mu pairs, so agreement also tests that fold.
  *
- * Build: gcc -O2 -fPIC -shared [-fopenmp] kitrt_oracle.c -lm
+ * Build: gcc -O3 -std=c99 -fPIC -shared [-fopenmp] kitrt_oracle.c -lm (ISO C mode: no floating-point
+ * contraction, so x86-64 and aarch64 hosts round identically).
  */
 #include <math.h>
 #include <stdint.h>
@@ -611,6 +613,67 @@ int orc_mn_run(int C, int n, int Q, const double *M, const double *w, const doub
 /* Discrete adjoint of the step                                                               */
 /* ------------------------------------------------------------------------------------------ */
 
+/* Transpose of the one-step map u^s -> u^{s+1} = u^s - dt/A F(psi(alpha(u^s))) + dt R(u^s),
+ * linearised at (u, alpha) with alpha the converged closure of u and psi its ansatz:
+ *   lamn = (du^{s+1}/du^s)^T lam.
+ * The flux term gives mu_cq = d(sum_c lam_c . u_c^{s+1}) / d psi_cq (transposed upwind gather);
+ * the closure term maps it back through d psi_iq / d u_i = psi_iq m_q^T H_i^-1 (implicit-function
+ * theorem on g(alpha, u) = <m exp(alpha.m)> - u = 0); the source Jacobian -sigma_t I + sigma_s
+ * e0 e0^T is symmetric. mu [C x Q] is scratch. Returns the number of Cholesky failures. */
+static int orc_step_transpose(int C, int n, int Q, const double *M, const double *w,
+                              const double *ox, const double *oy, const int32_t *nbr,
+                              const double *nrm, const double *area, const double *sa,
+                              const double *ss, double dt, int bc, const double *u,
+                              const double *al, const double *psi, const double *lam, double *mu,
+                              double *lamn)
+{
+    int nfail = 0;
+    /* mu_cq = d(sum_c lambda_c . u_c^{s+1}) / d psi_cq through the flux term */
+    for (size_t k = 0; k < (size_t)C * Q; ++k) mu[k] = 0.0;
+    for (int c = 0; c < C; ++c) {
+        const double *lc = lam + (size_t)c * n;
+        for (int k = 0; k < 3; ++k) {
+            int j = nbr[3 * c + k];
+            double nx = nrm[6 * c + 2 * k], ny = nrm[6 * c + 2 * k + 1];
+            for (int q = 0; q < Q; ++q) {
+                double dot = ox[q] * nx + oy[q] * ny;
+                double Lq = 0.0;
+                for (int a = 0; a < n; ++a) Lq += lc[a] * M[(size_t)q * n + a];
+                double coef = -dt / area[c] * w[q] * dot * Lq;
+                if (dot > 0.0)
+                    mu[(size_t)c * Q + q] += coef;
+                else if (j >= 0)
+                    mu[(size_t)j * Q + q] += coef;
+                else if (bc == 0)
+                    mu[(size_t)c * Q + q] += coef;
+            }
+        }
+    }
+    /* (du^{s+1}/du^s)^T lambda^{s+1} */
+    for (int i = 0; i < C; ++i) {
+        const double *li = lam + (size_t)i * n;
+        double *ln = lamn + (size_t)i * n;
+        /* identity + source Jacobian (-sigma_t I + sigma_s e0 e0^T, symmetric) */
+        for (int a = 0; a < n; ++a)
+            ln[a] = li[a] + dt * (-(sa[i] + ss[i]) * li[a] + (a == 0 ? ss[i] * li[0] : 0.0));
+        /* closure: H_i^-1 sum_q mu_iq psi_iq m_q */
+        double H[64 * 64], L[64 * 64], r[64], x[64];
+        orc_dual_eval(n, Q, M, w, u + (size_t)i * n, al + (size_t)i * n, NULL, NULL, H, NULL);
+        for (int a = 0; a < n; ++a) r[a] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            double t = mu[(size_t)i * Q + q] * psi[(size_t)i * Q + q];
+            for (int a = 0; a < n; ++a) r[a] += t * M[(size_t)q * n + a];
+        }
+        if (orc_cholesky(n, H, L) != 0) {
+            ++nfail;
+            continue;
+        }
+        orc_chol_solve(n, L, r, x);
+        for (int a = 0; a < n; ++a) ln[a] += x[a];
+    }
+    return nfail;
+}
+
 /* Objective: absorbed energy in the target cells,
  *   J = sum_{s=0}^{nsteps-1} dt sum_{i in T} A_i sigma_a,i <psi_i>,  <psi_i> = u_i0 / m_0.
  * Parameters: per-block sigma_a and sigma_s (block_of_cell). The reverse sweep applies the exact
@@ -677,50 +740,10 @@ int orc_mn_adjoint(int C, int n, int Q, const double *M, const double *w, const 
             dJ_dss[block_of_cell[i]] += -dt * lus;
             if (target[i]) dJ_dsa[block_of_cell[i]] += dt * area[i] * ui[0] / m0;
         }
-        /* mu_cq = d(sum_c lambda_c . u_c^{s+1}) / d psi_cq through the flux term */
-        for (size_t k = 0; k < (size_t)C * Q; ++k) mu[k] = 0.0;
-        for (int c = 0; c < C; ++c) {
-            const double *lc = lam + (size_t)c * n;
-            for (int k = 0; k < 3; ++k) {
-                int j = nbr[3 * c + k];
-                double nx = nrm[6 * c + 2 * k], ny = nrm[6 * c + 2 * k + 1];
-                for (int q = 0; q < Q; ++q) {
-                    double dot = ox[q] * nx + oy[q] * ny;
-                    double Lq = 0.0;
-                    for (int a = 0; a < n; ++a) Lq += lc[a] * M[(size_t)q * n + a];
-                    double coef = -dt / area[c] * w[q] * dot * Lq;
-                    if (dot > 0.0)
-                        mu[(size_t)c * Q + q] += coef;
-                    else if (j >= 0)
-                        mu[(size_t)j * Q + q] += coef;
-                    else if (bc == 0)
-                        mu[(size_t)c * Q + q] += coef;
-                }
-            }
-        }
-        /* lambda^s = dJ_s/du^s + (du^{s+1}/du^s)^T lambda^{s+1} */
-        for (int i = 0; i < C; ++i) {
-            const double *li = lam + (size_t)i * n;
-            double *ln = lamn + (size_t)i * n;
-            /* identity + source Jacobian (-sigma_t I + sigma_s e0 e0^T, symmetric) */
-            for (int a = 0; a < n; ++a)
-                ln[a] = li[a] + dt * (-(sa[i] + ss[i]) * li[a] + (a == 0 ? ss[i] * li[0] : 0.0));
-            /* closure: H_i^-1 sum_q mu_iq psi_iq m_q */
-            double H[64 * 64], L[64 * 64], r[64], x[64];
-            orc_dual_eval(n, Q, M, w, u + (size_t)i * n, al + (size_t)i * n, NULL, NULL, H, NULL);
-            for (int a = 0; a < n; ++a) r[a] = 0.0;
-            for (int q = 0; q < Q; ++q) {
-                double t = mu[(size_t)i * Q + q] * psi[(size_t)i * Q + q];
-                for (int a = 0; a < n; ++a) r[a] += t * M[(size_t)q * n + a];
-            }
-            if (orc_cholesky(n, H, L) != 0) {
-                ++nfail;
-                continue;
-            }
-            orc_chol_solve(n, L, r, x);
-            for (int a = 0; a < n; ++a) ln[a] += x[a];
-            if (target[i]) ln[0] += dt * area[i] * sa[i] / m0;
-        }
+        nfail += orc_step_transpose(C, n, Q, M, w, ox, oy, nbr, nrm, area, sa, ss, dt, bc, u, al,
+                                    psi, lam, mu, lamn);
+        for (int i = 0; i < C; ++i)
+            if (target[i]) lamn[(size_t)i * n] += dt * area[i] * sa[i] / m0;
         memcpy(lam, lamn, sizeof(double) * Cn);
     }
     free(us);
@@ -734,6 +757,63 @@ int orc_mn_adjoint(int C, int n, int Q, const double *M, const double *w, const 
     free(alpha);
     free(st);
     return nfail;
+}
+
+/* One-step transpose (vector-Jacobian product) at (u, alpha), alpha the converged closure of u:
+ * out = (du^{s+1}/du^s)^T lam, the reverse step of orc_mn_adjoint without the objective's terms.
+ * Returns the number of Cholesky failures. */
+int orc_step_vjp(int C, int n, int Q, const double *M, const double *w, const double *ox,
+                 const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+                 const double *sa, const double *ss, double dt, int bc, const double *u,
+                 const double *alpha, const double *lam, double *out)
+{
+    double *psi = (double *)malloc(sizeof(double) * (size_t)C * Q);
+    double *mu = (double *)malloc(sizeof(double) * (size_t)C * Q);
+    orc_ansatz(C, n, Q, M, alpha, psi, 0);
+    int nf = orc_step_transpose(C, n, Q, M, w, ox, oy, nbr, nrm, area, sa, ss, dt, bc, u, alpha, psi,
+                                lam, mu, out);
+    free(psi);
+    free(mu);
+    return nf;
+}
+
+/* One-step tangent (Jacobian-vector product) at (u, alpha), written in forward mode and
+ * independently of the transpose above: the closure's tangent d alpha_i = H_i^-1 du_i (from
+ * g(alpha, u) = 0), the ansatz's d psi_iq = psi_iq m_q . d alpha_i, then the step itself, which is
+ * linear in (psi, u) once the source q is zero:
+ *   out = du - dt/A F(d psi) + dt (-sigma_a du - sigma_s (du - du_0 e_0)).
+ * Returns the number of Cholesky failures. */
+int orc_step_jvp(int C, int n, int Q, const double *M, const double *w, const double *ox,
+                 const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+                 const double *sa, const double *ss, double dt, int bc, const double *u,
+                 const double *alpha, const double *du, double *out)
+{
+    double *dpsi = (double *)malloc(sizeof(double) * (size_t)C * Q);
+    double *zero = (double *)calloc((size_t)C, sizeof(double));
+    int nf = 0;
+    for (int i = 0; i < C; ++i) {
+        double H[64 * 64], L[64 * 64], da[64];
+        orc_dual_eval(n, Q, M, w, u + (size_t)i * n, alpha + (size_t)i * n, NULL, NULL, H, NULL);
+        if (orc_cholesky(n, H, L) != 0) {
+            ++nf;
+            for (int a = 0; a < n; ++a) da[a] = 0.0;
+        } else {
+            orc_chol_solve(n, L, du + (size_t)i * n, da);
+        }
+        for (int q = 0; q < Q; ++q) {
+            double z = 0.0, dz = 0.0;
+            for (int a = 0; a < n; ++a) {
+                z += alpha[(size_t)i * n + a] * M[(size_t)q * n + a];
+                dz += da[a] * M[(size_t)q * n + a];
+            }
+            dpsi[(size_t)i * Q + q] = exp(z) * dz;
+        }
+    }
+    memcpy(out, du, sizeof(double) * (size_t)C * n);
+    orc_flux_update(C, n, Q, M, w, ox, oy, nbr, nrm, area, dpsi, sa, ss, zero, dt, bc, out, 0);
+    free(dpsi);
+    free(zero);
+    return nf;
 }
 
 /* Forward value only of the same objective (for finite differences). */

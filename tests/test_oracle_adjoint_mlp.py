@@ -104,3 +104,60 @@ def test_adam_first_step_closed_form():
     v = np.zeros(10)
     O.adam(p, g, m, v, 1, lr=1e-2, eps=0.0)
     np.testing.assert_allclose(p, p0 - 1e-2 * np.sign(g), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_one_step_transpose_dot_product(bc):
+    """<J du, lam> = <du, J^T lam> for the one-step map u^s -> u^{s+1} at a converged closure, with
+    J du from the oracle's forward-mode tangent and J^T lam from the reverse step its adjoint
+    uses (two separately written code paths), to 1e-12 of |J du| |lam|; the tangent itself
+    agrees with central differences of the forward step."""
+    N, order = 2, 6
+    T = O.Tables(N, order)
+    m = synth.jittered_mesh(9, 0.0, 1.0, seed=5)
+    G = O.Geometry(m.xy, m.tri)
+    C = G.C
+    rng = np.random.default_rng(8)
+    mu, phi, w, ox, oy = O.quadrature(order)
+    c, k, wt = synth.vmf_mixtures(C, 12, kappa_hi=5.0)
+    u = synth.vmf_density(np.stack([ox, oy, mu], axis=1), c, k, wt) @ (T.w[:, None] * T.M)
+    alpha = O.isotropic_alpha(T, u)
+    st, _ = O.closure(T, u, alpha, tau=1e-13)
+    assert (st == 0).all()
+    sa, ss = rng.uniform(0, 1, C), rng.uniform(0, 1, C)
+    dt = G.cfl_dt(0.4)
+    du = rng.normal(size=u.shape) * np.abs(u).max() * 1e-2
+    lam = rng.normal(size=u.shape)
+    Jdu = O.step_jvp(T, G, u, alpha, sa, ss, dt, du, bc=bc)
+    JTl = O.step_vjp(T, G, u, alpha, sa, ss, dt, lam, bc=bc)
+    lhs, rhs = float(np.sum(Jdu * lam)), float(np.sum(du * JTl))
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Jdu) * np.linalg.norm(lam), (lhs, rhs)
+    # the tangent is the derivative of the forward step
+    h = 1e-4
+
+    def step(uu):
+        uu = uu.copy()
+        aa = alpha.copy()
+        nf, _ = O.mn_run(T, G, uu, aa, sa, ss, np.zeros(C), dt, 1, bc=bc, tau=1e-13)
+        assert nf == 0
+        return uu
+
+    fd = (step(u + h * du) - step(u - h * du)) / (2 * h)
+    assert np.linalg.norm(fd - Jdu) <= 1e-6 * np.linalg.norm(Jdu)
+
+
+def test_adam_second_step_closed_forms():
+    """Adam at t = 2 (Kingma & Ba): with the same gradient twice the bias-corrected moments are
+    exactly g and g^2, so each step is -lr sign(g); with the gradient reversed, m^_2 =
+    -(1 - b1)/(1 + b1) g and v^_2 = g^2, so the second step is +lr (1 - b1)/(1 + b1) sign(g).
+    A bias correction with the wrong power of beta at t >= 2 fails both."""
+    rng = np.random.default_rng(4)
+    lr, b1, b2 = 1e-2, 0.9, 0.999
+    g = rng.normal(size=12)
+    p0 = rng.normal(size=12)
+    for g2, expect in [(g, p0 - 2 * lr * np.sign(g)),
+                       (-g, p0 - lr * np.sign(g) + lr * (1 - b1) / (1 + b1) * np.sign(g))]:
+        p, m, v = p0.copy(), np.zeros(12), np.zeros(12)
+        O.adam(p, g, m, v, 1, lr=lr, b1=b1, b2=b2, eps=0.0)
+        O.adam(p, g2, m, v, 2, lr=lr, b1=b1, b2=b2, eps=0.0)
+        np.testing.assert_allclose(p, expect, rtol=0, atol=1e-15)

@@ -158,3 +158,120 @@ def test_line_source_mass_and_positivity():
     assert nf == 0
     assert abs(float((G.area * u[:, 0]).sum()) / mass0 - 1) < 1e-12
     assert (O.ansatz(T, alpha) > 0).all()
+
+
+def _numpy_rule_and_basis(N, order):
+    """The product rule and the real spherical harmonics built independently of the oracle:
+    numpy's Gauss-Legendre nodes, 2*order equally spaced azimuths, scipy's complex harmonics
+    turned real (Condon-Shortley phase removed), functions even in mu only."""
+    from scipy.special import sph_harm_y
+    x, wg = np.polynomial.legendre.leggauss(order)
+    nphi = 2 * order
+    pts = []
+    for mu, wk in zip(x, wg):
+        for l in range(1, nphi + 1):
+            pts.append((mu, 2 * math.pi * l / nphi, wk * 2 * math.pi / nphi))
+    mu = np.array([p[0] for p in pts])
+    phi = np.array([p[1] for p in pts])
+    w = np.array([p[2] for p in pts])
+    s = np.sqrt(1 - mu ** 2)
+    om = np.stack([s * np.sin(phi), s * np.cos(phi)], axis=1)
+    theta = np.arccos(mu)
+    cols, deg = [], []
+    for l in range(N + 1):
+        for k in range(-l, l + 1):
+            if (l + abs(k)) % 2:
+                continue
+            y = sph_harm_y(l, abs(k), theta, phi)
+            if k == 0:
+                cols.append(y.real)
+            elif k > 0:
+                cols.append(math.sqrt(2) * (-1) ** k * y.real)
+            else:
+                cols.append(math.sqrt(2) * (-1) ** abs(k) * y.imag)
+            deg.append(l)
+    return w, om, np.stack(cols, axis=1), np.array(deg)
+
+
+def _numpy_geometry(xy, tri):
+    """Counter-clockwise triangles, face k from vertex k to k+1, outward normal scaled by the
+    face length, neighbours by shared edges (brute force)."""
+    def cross(p, q):
+        return p[0] * q[1] - p[1] * q[0]
+
+    tri = [list(t) for t in tri]
+    for t in tri:
+        a, b, c = (np.array(xy[v]) for v in t)
+        if cross(b - a, c - a) < 0:
+            t[1], t[2] = t[2], t[1]
+    C = len(tri)
+    area = np.array([0.5 * abs(cross(np.array(xy[t[1]]) - xy[t[0]], np.array(xy[t[2]]) - xy[t[0]]))
+                     for t in tri])
+    nrm = np.zeros((C, 3, 2))
+    nbr = -np.ones((C, 3), dtype=int)
+    for c, t in enumerate(tri):
+        for k in range(3):
+            a, b = t[k], t[(k + 1) % 3]
+            nrm[c, k] = [xy[b][1] - xy[a][1], xy[a][0] - xy[b][0]]
+            for d, s in enumerate(tri):
+                if d != c and a in s and b in s:
+                    nbr[c, k] = d
+    return area, nrm, nbr
+
+
+def _eight_triangles():
+    xy = np.array([[i * 0.5, j * 0.5] for j in range(3) for i in range(3)])
+    tri = []
+    for j in range(2):
+        for i in range(2):
+            v0, v1, v2, v3 = j * 3 + i, j * 3 + i + 1, (j + 1) * 3 + i + 1, (j + 1) * 3 + i
+            tri += [[v0, v1, v2], [v0, v2, v3]]
+    return xy, np.array(tri, dtype=np.int32)
+
+
+@pytest.mark.parametrize("mesh", ["two", "eight"])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_kinetic_flux_of_the_pn_ansatz_is_the_half_range_matrix_flux(mesh, bc):
+    """The kinetic flux [Sec. 4.4] fed the quadratic-entropy (P_N) ansatz psi = u . m [Sec. 3.1]
+    becomes a matrix flux F_f = B+(n_f) u_i + B-(n_f) u_up with the half-range matrices
+    B+-(n) = sum_q w_q m_q m_q^T (Omega_q . n)^+- (so B+ + B- = n_x A_x + n_y A_y with the P_N
+    flux Jacobians A_l = <m m^T Omega_l>). The matrices, the rule, the basis and the geometry are
+    built here with numpy/scipy, independently of the oracle; the oracle's flux of u . m must
+    match to 1e-13. This pins the flux's orientation, upwinding and boundary ghosts."""
+    N, order = 3, 6
+    if mesh == "two":
+        xy = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+        tri = np.array([[0, 1, 2], [0, 3, 2]], dtype=np.int32)
+    else:
+        xy, tri = _eight_triangles()
+    T = O.Tables(N, order)
+    G = O.Geometry(xy, tri)
+    w, om, Mb, deg = _numpy_rule_and_basis(N, order)
+    area, nrm, nbr = _numpy_geometry(xy, tri)
+    C, n = len(tri), T.n
+    rng = np.random.default_rng(11)
+    u = rng.normal(size=(C, n))
+    # P_N flux Jacobians: symmetric, coupling degrees l and l +- 1 only
+    Ax = Mb.T @ (w[:, None] * om[:, :1] * Mb)
+    Ay = Mb.T @ (w[:, None] * om[:, 1:] * Mb)
+    for A in (Ax, Ay):
+        np.testing.assert_allclose(A, A.T, atol=1e-14)
+        assert np.abs(A[np.abs(deg[:, None] - deg[None, :]) != 1]).max() < 1e-14
+    F = np.zeros((C, n))
+    for c in range(C):
+        for k in range(3):
+            nv = nrm[c, k]
+            d = om @ nv
+            Bp = Mb.T @ (w[:, None] * np.maximum(d, 0)[:, None] * Mb)
+            Bm = Mb.T @ (w[:, None] * np.minimum(d, 0)[:, None] * Mb)
+            np.testing.assert_allclose(Bp + Bm, nv[0] * Ax + nv[1] * Ay, atol=1e-13)
+            assert np.linalg.eigvalsh(Bp).min() > -1e-13 and np.linalg.eigvalsh(Bm).max() < 1e-13
+            j = nbr[c, k]
+            up = u[j] if j >= 0 else (u[c] if bc == 0 else np.zeros(n))
+            F[c] += Bp @ u[c] + Bm @ up
+    # the oracle's kinetic flux of psi = u . m (dt = 1, no source terms): u - u' = F / A
+    psi = np.ascontiguousarray(u @ T.M.T)
+    uo = u.copy()
+    O.flux_update(T, G, psi, uo, np.zeros(C), np.zeros(C), np.zeros(C), 1.0, bc=bc)
+    got = (u - uo) * G.area[:, None]
+    assert np.abs(got - F).max() <= 1e-13 * max(1.0, np.abs(F).max())
