@@ -148,9 +148,14 @@ int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_
 
 /* Work accounting of one cell evaluation of the dual (one quadrature pass) in the solver's mode:
  * moments n, degree-2N moments n2, folded points Q', non-zero Gaunt coefficients, and
- *   sweep_fp64_flops   FP64 flops of the quadrature sweep without exp: 2nQ' (exponents) + Q'
- *                      (weights) + 2 n2 Q' (FP64 mode: all moments) or 2 n Q' (mixed modes:
- *                      gradient moments only);
+ *   sweep_fp64_flops   FP64 flops (FMA = 2) of the quadrature sweep without exp, in its
+ *                      sum-factorised form over pairs of mirrored azimuths and rings of equal
+ *                      |mu|: per pair (Q'/2 of them) the exponents (2N - 1 operations) and the
+ *                      azimuthal sums up to degree L (L = N in the mixed modes, whose higher
+ *                      moments run on tensor cores; L = 2N in FP64 mode), per ring the exponent
+ *                      coefficients (n FMA) and the moments (nmom(L) FMA);
+ *   sweep_fp64_ops     FP64-pipe instructions of the same sweep including the exponentials
+ *                      (9 per exp on the common path of the table-driven method);
  *   exps               exponentials per evaluation (Q');
  *   tensor_flops       mixed modes: 3 x 2 (n2 - n) Q' on tensor cores (three split products);
  *   newton_flops       the per-cell Newton step: 2 nnz (Hessian) + n^3/3 + 2n^2 (Cholesky,
@@ -161,6 +166,7 @@ typedef struct {
     double exps;
     double tensor_flops;
     double newton_flops;
+    double sweep_fp64_ops;
 } kitrt_work;
 int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out);
 

@@ -16,6 +16,7 @@
 #include "kitrt_internal.cuh"
 #include "kexp.cuh"
 #include "newton_common.cuh"
+#include "sweep.cuh"
 
 namespace {
 
@@ -293,6 +294,68 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
 }
 
 // ---------------------------------------------------------------------------------------------
+// FP64 sweep of the FP64 mode: one thread per listed cell (tiles of 128), every degree-2N moment
+// in the sum-factorised form of sweep.cuh. Work items are (tile, part of the quadrature); each
+// stores its partial moments with plain stores into its own column block of Vacc, which the
+// Newton kernel adds in order, so the result does not depend on scheduling.
+// ---------------------------------------------------------------------------------------------
+constexpr int kSweepThreads = 128;
+
+template <int NN>
+__global__ void __launch_bounds__(kSweepThreads)
+sweep64_kernel(Tables T, NewtonState S, int k, double *__restrict__ Vacc, int vs, int target_items)
+{
+    constexpr int n = Dims<NN>::n, n2 = Dims<NN>::n2, NA = 2 * NN + 1, NB = 4 * NN + 1;
+    constexpr int TW = 4 * NN + 1;
+    __shared__ double sV[n2 * kSweepThreads];  // [n2][thread]
+    const int32_t *list_in = S.list[k & 1];
+    const int cnt_in = S.cnt[k % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.cnt[(k + 2) % 3] = 0;
+    const int nunits = T.Qp / 32;
+    const SweepSplit sp = sweep_split(cnt_in, target_items, nunits);
+    const int items = sp.tiles * sp.parts;
+    double *mine = sV + threadIdx.x;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int tile = item / sp.parts, part = item % sp.parts;
+        const int slot = tile * kSweepThreads + threadIdx.x;
+        if (slot >= cnt_in) continue;  // threads are independent: no block barrier below
+        const int p_begin = part * sp.units_per_part * 16;
+        const int p_end = min(nunits, (part + 1) * sp.units_per_part) * 16;
+        const int cell = list_in[slot];
+        const size_t off = (size_t)cell * n;
+        const int ph = S.phase[cell];
+        const double lam = ph == PH_NEWTON ? S.lam[cell] : 0.0;
+        double at[n], A[NA], B[NB];
+#pragma unroll
+        for (int a = 0; a < n; ++a) {
+            const double al = S.alpha[off + a];
+            at[a] = ph == PH_NEWTON ? fma(lam, S.dir[off + a], al) : al;
+        }
+#pragma unroll
+        for (int c = 0; c < n2; ++c) mine[c * kSweepThreads] = 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) B[j] = 0.0;
+        auto V = [&](int c) -> double & { return mine[c * kSweepThreads]; };
+        int ring = -1;
+        for (int pr = p_begin; pr < p_end; ++pr) {
+            const int rg = pr < T.npair ? pr / T.P : T.R;
+            if (rg != ring) {
+                if (ring >= 0) ring_flush<2 * NN>(T.ringWP + (size_t)ring * n2, B, V);
+                ring_coeffs<NN>(at, T.ringP + (size_t)rg * n2, A);
+                ring = rg;
+            }
+            double e1, e2;
+            pair_eval<NN, 2 * NN>(A, T.ptrig + (size_t)pr * TW, pr < T.npair && pr % T.P == 0,
+                                  T.exptab, B, e1, e2);
+        }
+        if (ring >= 0) ring_flush<2 * NN>(T.ringWP + (size_t)ring * n2, B, V);
+        double *col = Vacc + (size_t)part * cnt_in + slot;
+#pragma unroll
+        for (int c = 0; c < n2; ++c) col[(size_t)c * vs] = mine[c * kSweepThreads];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // finish: final alpha (alpha_k plus the polish step if enabled) to the caller, and optionally the
 // ansatz psi at every folded point (FP64 and/or FP32).
 // ---------------------------------------------------------------------------------------------
@@ -460,7 +523,8 @@ int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, cons
     if (blocks > mn->nsm * 32) blocks = mn->nsm * 32;
     LaunchScope ls(mn, PK_POST, s, 0);
     const int mixed = mn->p.mode != KITRT_FP64;
-    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, kPostBlock, 0, s>>>(T, S, u, k, np, Vacc, mn->mesh->C, mixed));
+    const int target = mixed ? mn->target_mixed : mn->target_fp64;
+    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, kPostBlock, 0, s>>>(T, S, u, k, np, Vacc, mn->vs, mixed, target));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
@@ -507,6 +571,24 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
+// Grid of the FP64 sweep: as many CTAs as are resident on all SMs at once.
+int fp64_sweep_grid(const kitrt_mn *mn)
+{
+    int resident = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (mn->N) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<1>, kSweepThreads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<2>, kSweepThreads, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<3>, kSweepThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<4>, kSweepThreads, 0); break;
+    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<5>, kSweepThreads, 0); break;
+    default: break;
+    }
+    if (e != cudaSuccess || resident < 1) resident = 1;
+    if (resident > 8) resident = 8;
+    return mn->nsm * resident;
+}
+
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s, bool filter,
                      float *psi32, double *Vacc)
@@ -517,9 +599,10 @@ int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
         // fused sweep: no accumulator (the caller may pass a launch-only view without a mesh)
         KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false, true><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc, 0)));
     } else if (filter) {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc, mn->mesh->C)));
+        // cells handed to the FP64 Hessian: whole sums into part 0 of their list slots
+        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, true, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc, mn->vs)));
     } else {
-        KITRT_DISPATCH_N(mn->N, (eval_kernel<NN, false, false><<<grid, kWarps * 32, 0, s>>>(T, S, u, k, np, psi32, Vacc, mn->mesh->C)));
+        KITRT_DISPATCH_N(mn->N, (sweep64_kernel<NN><<<mn->grid_fp64, kSweepThreads, 0, s>>>(T, S, k, Vacc, mn->vs, mn->target_fp64)));
     }
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }

@@ -4,20 +4,22 @@
 // against the degree-2N basis (H_ab = sum_c G_abc V_c, Gaunt coefficients G). Its first n
 // moments are the gradient's <m e> and stay in FP64; the remaining n2 - n moments enter only the
 // Hessian and are a batched dense contraction
-//     V_hi[cells x (n2-n)] = E[cells x Q'] . M_hi[Q' x (n2-n)],   E = w exp(alpha.m)
+//     V_hi[cells x (n2-n)] = E[cells x Q'] . (w M_hi)[Q' x (n2-n)],   E = exp(alpha.m)
 // that runs on the 5th-generation tensor cores: tcgen05.mma with TF32 (kind::tf32) or BF16
-// (kind::f16) operands and FP32 accumulation in tensor memory. Exponents, exp, the gradient, the
+// (kind::f16) operands and FP32 accumulation in tensor memory (the quadrature weights are folded
+// into the basis table). Exponents, exp and the gradient moments run in FP64 in the
+// sum-factorised form of sweep.cuh (pairs of mirrored azimuths, coefficients per ring); the
 // objective, the Cholesky factorisation and the line search stay in FP64 (newton_post).
 //
 // One CTA (256 threads) owns a tile of 128 listed cells (the MMA's M = 128 rows, row = cell).
-// The quadrature runs in chunks of 32 points: every thread computes E for one row and 16 points
-// in FP64, accumulates its FP64 gradient moments, and stores E rounded to TF32/BF16 into shared
-// memory in the canonical K-major core-matrix layout (8 rows x 16 bytes per core matrix, no
-// swizzle); the threads also stage the matching 32 columns of M_hi. One elected thread issues
-// the MMAs of the chunk and commits them to an mbarrier; chunks alternate between two buffers so
-// that the next chunk's FP64 work overlaps the tensor-core work of the previous one. Every wait
-// is bounded: on expiry the kernel records KITRT_ETIMEOUT, drains what it issued (bounded) and
-// frees its tensor memory.
+// The quadrature runs in chunks of 16 pairs (32 points): every thread evaluates 8 pairs of one
+// row in FP64, accumulates its FP64 gradient moments, and stores E rounded to TF32/BF16 into
+// shared memory in the canonical K-major core-matrix layout (8 rows x 16 bytes per core matrix,
+// no swizzle); the threads also stage the matching 32 columns of the weighted M_hi. One elected
+// thread issues the MMAs of the chunk and commits them to an mbarrier; chunks alternate between
+// two buffers so that the next chunk's FP64 work overlaps the tensor-core work of the previous
+// one. Every wait is bounded: on expiry the kernel records KITRT_ETIMEOUT, drains what it issued
+// (bounded) and frees its tensor memory.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -25,6 +27,7 @@
 #include "kitrt_internal.cuh"
 #include "kexp.cuh"
 #include "newton_common.cuh"
+#include "sweep.cuh"
 
 namespace {
 
@@ -191,27 +194,28 @@ struct MixedSmem {
 };
 
 // Work item = (tile of 128 listed cells, range of quadrature chunks). When few cells are listed
-// (the later sweeps of a closure), each tile's quadrature range is split over several CTAs so
-// that every SM gets work; the partial moments of a work item are added into Vacc (one FP64 row
-// of n2 moments per list position: entry c of slot j at Vacc[c vs_c + j vs_s], [n2 x C] columns
-// for the Newton sweeps, [C x n2] rows for the moments of given alphas) with atomics, and the
-// post kernel finishes the Newton logic.
+// (the later sweeps of a closure), each tile's quadrature range is split over several CTAs
+// (sweep_split) so that every SM gets work; each work item stores its partial moments with plain
+// stores into its own column block of Vacc (entry c of list slot j, part p at
+// Vacc[c vs_c + (p cnt + j) vs_s]; [n2 x vs] columns for the Newton sweeps, [C x n2] rows and one
+// part for the moments of given alphas), and the Newton kernel adds the parts in order.
 template <int NN, bool BF16, bool MOMENTS_ONLY>
 __global__ void __launch_bounds__(kThreads, 1)
 eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                   const double *__restrict__ alpha_in, double *__restrict__ Vacc, int vs_c, int vs_s,
-                  int C,
-                  int target_items, float *__restrict__ psi32)
+                  int C, int target_items, float *__restrict__ psi32)
 {
     using D = MixedDims<NN>;
     using L = MixedSmem<NN, BF16>;
-    constexpr int n = D::n, n2 = D::n2, NP = D::NP;
+    constexpr int n = D::n, n2 = D::n2, NP = D::NP, NA = 2 * NN + 1;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = (uint64_t *)(smem + L::off_bar);
     uint32_t *tmem_slot = (uint32_t *)(smem + L::off_bar + 16);
     int *abort_flag = (int *)(smem + L::off_bar + 24);
+    double *sU = (double *)(smem + L::off_V);  // [n][128]: the second half's gradient moments
     const int tid = threadIdx.x, warp = tid >> 5;
     const int Qp = T.Qp, nchunks = Qp / kChunk;
+    constexpr int TW = 4 * NN + 1;  // ptrig row width
 
     int cnt_in;
     const int32_t *list_in = nullptr;
@@ -222,12 +226,9 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
         cnt_in = S.cnt[k % 3];
         if (blockIdx.x == 0 && tid == 0) S.cnt[(k + 2) % 3] = 0;
     }
-    const int tiles = (cnt_in + kTileM - 1) / kTileM;
-    int ks = tiles > 0 ? (target_items + tiles - 1) / tiles : 1;
-    ks = ks < 1 ? 1 : (ks > nchunks ? nchunks : ks);
-    const int cpp = (nchunks + ks - 1) / ks;  // chunks per part
-    ks = (nchunks + cpp - 1) / cpp;
-    const int items = tiles * ks;
+    const SweepSplit sp = sweep_split(cnt_in, target_items, nchunks);
+    const int ks = sp.parts, cpp = sp.units_per_part;
+    const int items = sp.tiles * ks;
     if ((int)blockIdx.x >= items) return;  // no work item for this CTA (uniform per CTA)
 
     if (tid == 0) {
@@ -254,12 +255,14 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
         if (r < rows) cell = MOMENTS_ONLY ? base + r : list_in[base + r];
         bool active = cell >= 0;
         if (!MOMENTS_ONLY && active && S.h64[cell]) active = false;  // done by the FP64 sweep
-        double at[n], U[n];
+        double at[n], U[n], A[NA], B[NA];
 #pragma unroll
         for (int a = 0; a < n; ++a) {
             U[a] = 0.0;
             at[a] = 0.0;
         }
+#pragma unroll
+        for (int j = 0; j < NA; ++j) A[j] = B[j] = 0.0;
         if (active) {
             if (MOMENTS_ONLY) {
 #pragma unroll
@@ -274,6 +277,7 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                 }
             }
         }
+        int ring = -1;  // ring whose azimuthal sums B holds (uniform within a warp)
         for (int c = c_begin; c < c_end; ++c) {
             const int b = c & 1;
             unsigned char *Ahi = smem + L::off_Ahi(b), *Alo = smem + L::off_Alo(b);
@@ -287,36 +291,41 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                 if (*abort_flag) break;  // uniform: read after the barrier
             }
             tc_fence_after();
-            // FP64 part: exponent, exp, weight, gradient moments; E to the operand tile
-            const int q0 = c * kChunk + h * (kChunk / 2);
-#pragma unroll 4
-            for (int j = 0; j < kChunk / 2; ++j) {
-                const int q = q0 + j;
-                double e = 0.0;
-                if (active) {
-                    double z = 0.0;
-#pragma unroll
-                    for (int a = 0; a < n; ++a) z = fma(at[a], T.Mt[a * Qp + q], z);
-                    const double ez = kexp(z, T.exptab);
-                    // ansatz of the trial point (the last accepted trial leaves the solution's)
-                    if (psi32) psi32[(size_t)cell * Qp + q] = (float)ez;
-                    e = T.w[q] * ez;
-#pragma unroll
-                    for (int a = 0; a < n; ++a) U[a] = fma(e, T.Mt[a * Qp + q], U[a]);
+            // FP64 part: 8 pairs of this row (exponents, exp, gradient sums); E to the operand
+#pragma unroll 2
+            for (int i = 0; i < kChunk / 4; ++i) {
+                const int pr = c * (kChunk / 2) + h * (kChunk / 4) + i;
+                const int rg = pr < T.npair ? pr / T.P : T.R;
+                if (rg != ring) {
+                    if (ring >= 0)
+                        ring_flush<NN>(T.ringWP + (size_t)ring * n2, B, [&](int cc) -> double & { return U[cc]; });
+                    ring_coeffs<NN>(at, T.ringP + (size_t)rg * n2, A);
+                    ring = rg;
                 }
-                const int kk = h * (kChunk / 2) + j;
-                const float ef = (float)e;
-                if (BF16) {
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(ef);
-                    const __nv_bfloat16 lo = __float2bfloat16_rn(ef - __bfloat162float(hi));
-                    *(__nv_bfloat16 *)(Ahi + L::elem_off(r, kk)) = hi;
-                    *(__nv_bfloat16 *)(Alo + L::elem_off(r, kk)) = lo;
-                } else {
-                    uint32_t hi, lo;
-                    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(ef));
-                    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(ef - __uint_as_float(hi)));
-                    *(uint32_t *)(Ahi + L::elem_off(r, kk)) = hi;
-                    *(uint32_t *)(Alo + L::elem_off(r, kk)) = lo;
+                double e1 = 0.0, e2 = 0.0;
+                if (active) {
+                    pair_eval<NN, NN>(A, T.ptrig + (size_t)pr * TW, pr < T.npair && pr % T.P == 0,
+                                      T.exptab, B, e1, e2);
+                    // ansatz of the trial point (the last accepted trial leaves the solution's)
+                    if (psi32)
+                        *(float2 *)(psi32 + (size_t)cell * Qp + 2 * pr) = make_float2((float)e1, (float)e2);
+                }
+                const int kk = h * (kChunk / 2) + 2 * i;
+                const float ef[2] = {(float)e1, (float)e2};
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    if (BF16) {
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(ef[o]);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn(ef[o] - __bfloat162float(hi));
+                        *(__nv_bfloat16 *)(Ahi + L::elem_off(r, kk + o)) = hi;
+                        *(__nv_bfloat16 *)(Alo + L::elem_off(r, kk + o)) = lo;
+                    } else {
+                        uint32_t hi, lo;
+                        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(ef[o]));
+                        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(ef[o] - __uint_as_float(hi)));
+                        *(uint32_t *)(Ahi + L::elem_off(r, kk + o)) = hi;
+                        *(uint32_t *)(Alo + L::elem_off(r, kk + o)) = lo;
+                    }
                 }
             }
             // stage the chunk of the split table (row-major [2][NP x Qp] in global: high part,
@@ -324,11 +333,11 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
             constexpr int per16 = L::T;  // elements per 16 bytes
             constexpr int pieces = NP * (kChunk / per16);
             for (int p = tid; p < 2 * pieces; p += kThreads) {
-                const int part = p / pieces, pp = p % pieces;
+                const int hl = p / pieces, pp = p % pieces;
                 const int row = pp / (kChunk / per16), kp = (pp % (kChunk / per16)) * per16;
                 const uint4 v = *(const uint4 *)((const unsigned char *)Mhi +
-                                                 (((size_t)part * NP + row) * Qp + c * kChunk + kp) * L::esz);
-                *(uint4 *)((part ? Blo : Bhi) + L::elem_off(row, kp)) = v;
+                                                 (((size_t)hl * NP + row) * Qp + c * kChunk + kp) * L::esz);
+                *(uint4 *)((hl ? Blo : Bhi) + L::elem_off(row, kp)) = v;
             }
             fence_async_smem();
             __syncthreads();
@@ -350,6 +359,7 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
             }
             ++commits[b];
         }
+        if (ring >= 0) ring_flush<NN>(T.ringWP + (size_t)ring * n2, B, [&](int cc) -> double & { return U[cc]; });
         // drain: every MMA of this tile has completed once both buffers' last commits have
         if (tid == 0)
             for (int b = 0; b < 2 && !*abort_flag; ++b)
@@ -362,27 +372,32 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                 }
         if (tid != 0)
             for (int b = 0; b < 2; ++b) waited[b] = commits[b];
+        // the second half hands its gradient moments to the first
+        if (h == 1) {
+#pragma unroll
+            for (int a = 0; a < n; ++a) sU[a * kTileM + r] = U[a];
+        }
         __syncthreads();
         tc_fence_after();
         if (*abort_flag) break;
-        // partial moments of this work item into the accumulator row of its list position: the
-        // FP64 gradient moments from both halves, the tensor-core moments from TMEM (warps 0-3)
-        if (r < rows && (MOMENTS_ONLY || active)) {
-            double *row = Vacc + (size_t)(base + r) * vs_s;
+        // partial moments of this work item into its column of the accumulator: the FP64
+        // gradient moments of both halves, the tensor-core moments from TMEM (warps 0-3)
+        const bool store = r < rows && (MOMENTS_ONLY || active);
+        double *row = Vacc + ((size_t)part * cnt_in + base + r) * vs_s;
+        if (h == 0 && store) {
 #pragma unroll
-            for (int a = 0; a < n; ++a) atomicAdd(row + (size_t)a * vs_c, U[a]);
+            for (int a = 0; a < n; ++a) row[(size_t)a * vs_c] = U[a] + sU[a * kTileM + r];
         }
         if (h == 0) {
             const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-            double *row = Vacc + (size_t)(base + r) * vs_s;
 #pragma unroll
             for (int c0 = 0; c0 < NP; c0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
-                if (r < rows && (MOMENTS_ONLY || active)) {
+                if (store) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
-                        if (c0 + i < n2 - n) atomicAdd(row + (size_t)(n + c0 + i) * vs_c, (double)v[i]);
+                        if (c0 + i < n2 - n) row[(size_t)(n + c0 + i) * vs_c] = (double)v[i];
                 }
             }
         }
@@ -411,15 +426,11 @@ int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const
 {
     using L = MixedSmem<NN, BF16>;
     if (ensure_dyn_smem(eval_mixed_kernel<NN, BF16, MO>, L::total)) return KITRT_ECUDA;
-    // persistent grid of one CTA per SM; aim at two work items per CTA
-    const int tiles = (C + kTileM - 1) / kTileM;
-    const int grid = tiles < mn->nsm ? (tiles > 0 ? tiles : 1) : mn->nsm;
-    const int target = 2 * mn->nsm;
+    // persistent grid of one CTA per SM; aim at two work items per CTA (the moments of given
+    // alphas take one part per tile: rows of Vout are written whole)
     eval_mixed_kernel<NN, BF16, MO><<<mn->nsm, kThreads, L::total, s>>>(
         T, S, k, BF16 ? (const void *)mn->d_Mhi16 : (const void *)mn->d_Mhi32, alpha_in, Vacc,
-        MO ? 1 : mn->mesh->C, MO ? Dims<NN>::n2 : 1, C, target,
-        psi32);
-    (void)grid;
+        MO ? 1 : mn->vs, MO ? Dims<NN>::n2 : 1, C, MO ? 0 : mn->target_mixed, psi32);
     if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
     (void)u;
     (void)np;

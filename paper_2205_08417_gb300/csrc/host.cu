@@ -97,9 +97,18 @@ int basis2d(int L, double mu, double phi, double *out)
 int nmom_of(int L) { return (L + 1) * (L + 2) / 2; }
 
 // Folded product rule: pairs of Gauss nodes +-mu share the 2D direction and every basis value,
-// so they merge into one point of doubled weight (an odd order keeps mu = 0 once).
+// so they merge into one point of doubled weight (an odd order keeps mu = 0 once). Each ring (one
+// |mu|) has nphi = 2 order equally spaced azimuths phi_l = l 2 pi / nphi, l = 1..nphi, stored as
+// P = nphi / 2 pairs of points: pair 0 = (phi = 2 pi, phi = pi), the two azimuths whose sines
+// vanish; pair j >= 1 = (phi_j, phi_{nphi-j} = 2 pi - phi_j), a direction and its mirror image,
+// whose cosines are equal and whose sines are opposite. Pairs of a ring are consecutive, and
+// the two points of a pair are consecutive.
 struct FoldedRule {
-    std::vector<double> mu, phi, w;
+    std::vector<double> mu, phi, w;  // per point
+    std::vector<int> kind;           // per point: 0 first of a mirror pair, 1 its mirror,
+                                     // 2 phi = 0 (= 2 pi), 3 phi = pi
+    std::vector<double> ring_mu, ring_w;  // per ring: |mu| and the weight of each of its points
+    int nphi = 0, P = 0;
 };
 
 FoldedRule folded_rule(int order)
@@ -108,17 +117,62 @@ FoldedRule folded_rule(int order)
     gauss_legendre(order, x, gw);
     const int nphi = 2 * order, half = order / 2;
     FoldedRule r;
+    r.nphi = nphi;
+    r.P = nphi / 2;
     auto add_ring = [&](double mu, double wk) {
-        for (int l = 1; l <= nphi; ++l) {
+        const double wpt = wk * 2.0 * kPi / nphi;
+        r.ring_mu.push_back(mu);
+        r.ring_w.push_back(wpt);
+        auto add = [&](double phi, int kind) {
             r.mu.push_back(mu);
-            r.phi.push_back(l * (2.0 * kPi / nphi));
-            r.w.push_back(wk * 2.0 * kPi / nphi);
+            r.phi.push_back(phi);
+            r.w.push_back(wpt);
+            r.kind.push_back(kind);
+        };
+        add(2.0 * kPi, 2);
+        add(kPi, 3);
+        for (int j = 1; j < nphi / 2; ++j) {
+            add(j * (2.0 * kPi / nphi), 0);
+            add((nphi - j) * (2.0 * kPi / nphi), 1);
         }
     };
     // nodes are ascending: k = order-1 .. order-half are the positive ones, paired with order-1-k
     for (int k = order - 1; k >= order - half; --k) add_ring(x[k], gw[k] + gw[order - 1 - k]);
     if (order % 2) add_ring(0.0, gw[half]);
     return r;
+}
+
+// Azimuthal factor T_k(phi) of the real harmonics: 1 (k = 0), sqrt2 cos(k phi) (k > 0),
+// sqrt2 sin(|k| phi) (k < 0), with the symmetries of the pairs made exact: the mirror point takes
+// the first point's values with the sines negated, and phi = 0 and phi = pi take exact values.
+// For a mirror point (kind 1) `phi` is the azimuth of its pair's first point.
+double trig_factor(int k, double phi, int kind)
+{
+    const int ak = k < 0 ? -k : k;
+    if (kind == 2 || kind == 3) {
+        if (k < 0) return 0.0;
+        const double c = (kind == 3 && (ak & 1)) ? -1.0 : 1.0;
+        return k == 0 ? 1.0 : sqrt(2.0) * c;
+    }
+    if (k == 0) return 1.0;
+    if (k > 0) return sqrt(2.0) * cos(ak * phi);
+    const double s = sqrt(2.0) * sin(ak * phi);
+    return kind == 1 ? -s : s;
+}
+
+// The degree-L basis at a point of the folded rule: m_c = N_l^|k| P_l^|k|(mu) T_k(phi).
+int basis2d_rule(int L, double mu, double phi, int kind, double *out)
+{
+    double Pn[24][24];
+    norm_legendre(L, mu, Pn);
+    int i = 0;
+    for (int l = 0; l <= L; ++l)
+        for (int k = -l; k <= l; ++k) {
+            const int ak = k < 0 ? -k : k;
+            if ((l + ak) % 2) continue;
+            out[i++] = Pn[l][ak] * trig_factor(k, phi, kind);
+        }
+    return i;
 }
 
 template <typename T>
@@ -191,6 +245,12 @@ Tables kitrt_mn::tables() const
     T.wox32 = d_wox32;
     T.woy32 = d_woy32;
     T.exptab = d_exptab;
+    T.R = R;
+    T.P = P;
+    T.npair = Qf / 2;
+    T.ptrig = d_ptrig;
+    T.ringP = d_ringP;
+    T.ringWP = d_ringWP;
     return T;
 }
 
@@ -407,8 +467,20 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     double tmp[128];
     for (int q = 0; q < Qf; ++q) {
         double s = sqrt(1.0 - r.mu[q] * r.mu[q]);
-        double ox = s * sin(r.phi[q]), oy = s * cos(r.phi[q]);
-        basis2d(2 * mn->N, r.mu[q], r.phi[q], tmp);
+        // sin(phi), cos(phi) with the pairs' exact symmetries (a mirror point uses the azimuth
+        // of its pair's first point, the one before it)
+        const double phi0 = r.kind[q] == 1 ? r.phi[q - 1] : r.phi[q];
+        double sp, cp;
+        if (r.kind[q] == 2) {
+            sp = 0.0, cp = 1.0;
+        } else if (r.kind[q] == 3) {
+            sp = 0.0, cp = -1.0;
+        } else {
+            sp = r.kind[q] == 1 ? -sin(phi0) : sin(phi0);
+            cp = cos(phi0);
+        }
+        double ox = s * sp, oy = s * cp;
+        basis2d_rule(2 * mn->N, r.mu[q], phi0, r.kind[q], tmp);
         for (int c = 0; c < n2; ++c) Mt[(size_t)c * Qp + q] = tmp[c];
         for (int a = 0; a < n; ++a) mn->h_M[(size_t)q * n + a] = tmp[a];
         w[q] = r.w[q];
@@ -470,7 +542,8 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     };
     for (int c = 0; c < nhi; ++c)
         for (int q = 0; q < Qp; ++q) {
-            const double x = Mt[(size_t)(n + c) * Qp + q];
+            // the quadrature weight is folded into the table: the tensor cores take exp(alpha.m)
+            const double x = w[q] * Mt[(size_t)(n + c) * Qp + q];
             const float hi = tf32((float)x);
             Mhi32[(size_t)c * Qp + q] = hi;
             Mhi32[((size_t)NP + c) * Qp + q] = tf32((float)(x - (double)hi));
@@ -506,6 +579,36 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     std::vector<double> exptab(256);
     for (int j = 0; j < 256; ++j) exptab[j] = (double)exp2l((long double)j / 256.0L);
     TRY(dev_upload(mn, &mn->d_exptab, exptab));
+    // sum-factorised sweeps: azimuthal factors per pair and Legendre factors per ring
+    {
+        const int L2 = 2 * mn->N, TW = 2 * L2 + 1;
+        mn->R = (int)r.ring_mu.size();
+        mn->P = r.P;
+        std::vector<double> ptrig((size_t)(Qp / 2) * TW, 0.0);
+        for (int pr = 0; pr < Qf / 2; ++pr) {
+            const int q = 2 * pr;
+            const bool zero_pi = r.kind[q] == 2;
+            for (int k = 0; k <= L2; ++k)
+                ptrig[(size_t)pr * TW + k] = trig_factor(k, r.phi[q], zero_pi ? 2 : 0);
+            for (int k = 1; k <= L2; ++k)
+                ptrig[(size_t)pr * TW + L2 + k] =
+                    zero_pi ? trig_factor(k, r.phi[q], 3) : trig_factor(-k, r.phi[q], 0);
+        }
+        std::vector<double> ringP((size_t)(mn->R + 1) * n2, 0.0), ringWP((size_t)(mn->R + 1) * n2, 0.0);
+        for (int rg = 0; rg < mn->R; ++rg) {
+            double Pn[24][24];
+            norm_legendre(2 * mn->N, r.ring_mu[rg], Pn);
+            int c = 0;
+            for (int l = 0; l <= 2 * mn->N; ++l)
+                for (int k = -l; k <= l; k += 2, ++c) {
+                    ringP[(size_t)rg * n2 + c] = Pn[l][k < 0 ? -k : k];
+                    ringWP[(size_t)rg * n2 + c] = r.ring_w[rg] * Pn[l][k < 0 ? -k : k];
+                }
+        }
+        TRY(dev_upload(mn, &mn->d_ptrig, ptrig));
+        TRY(dev_upload(mn, &mn->d_ringP, ringP));
+        TRY(dev_upload(mn, &mn->d_ringWP, ringWP));
+    }
     TRY(dev_upload(mn, &mn->d_Mhi32, Mhi32));
     TRY(dev_upload(mn, &mn->d_Mhi16, Mhi16));
 
@@ -537,8 +640,15 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
         return KITRT_ECUDA;
     }
     TRY(dev_alloc(mn, &mn->d_psi, C * Qp));
-    TRY(dev_alloc(mn, &mn->d_Vacc, C * (size_t)n2));
-    if (cudaMemset(mn->d_Vacc, 0, sizeof(double) * C * (size_t)n2) != cudaSuccess) {
+    // sweep work split (sweep.cuh): the tensor-core sweep runs one CTA per SM and aims at two
+    // work items per CTA; the FP64 sweep fills the SMs with resident CTAs. A split never needs
+    // more than C + target * 128 columns per moment.
+    mn->target_mixed = 2 * mn->nsm;
+    mn->grid_fp64 = fp64_sweep_grid(mn);
+    mn->target_fp64 = mn->grid_fp64;
+    mn->vs = (int)C + 128 * std::max(mn->target_mixed, mn->target_fp64) + 128;
+    TRY(dev_alloc(mn, &mn->d_Vacc, (size_t)mn->vs * n2));
+    if (cudaMemset(mn->d_Vacc, 0, sizeof(double) * (size_t)mn->vs * n2) != cudaSuccess) {
         kitrt_mn_destroy(mn);
         return KITRT_ECUDA;
     }
@@ -591,13 +701,21 @@ int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_
 int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out)
 {
     if (!mn || !out) return KITRT_EINVAL;
-    const double n = mn->n, n2 = mn->n2, Qf = mn->Qf;
+    const double n = mn->n, n2 = mn->n2, Qf = mn->Qf, N = mn->N;
     const bool fp64 = mn->p.mode == KITRT_FP64;
     out->nmom = mn->n;
     out->nmom2 = mn->n2;
     out->nquad_folded = mn->Qf;
     out->gaunt_nnz = mn->gaunt_nnz;
-    out->sweep_fp64_flops = 2 * n * Qf + Qf + 2 * (fp64 ? n2 : n) * Qf;
+    // sum-factorised sweep (sweep.cuh), per pair of points: exponent C (N FMA) and S (1 MUL +
+    // N-1 FMA), z = C +- S (2), e +- e' (2), azimuthal sums up to degree L (1 ADD + 2L FMA);
+    // per ring: the exponent coefficients (n FMA) and the moments (nmom(L) FMA). FMA = 2 flops.
+    const double L = fp64 ? 2 * N : N, nout = fp64 ? n2 : n;
+    const double pairs = Qf / 2, rings = mn->R;
+    const double pair_ops = N + N + 2 + 2 + 1 + 2 * L, pair_fmas = N + (N - 1) + 2 * L;
+    const double ring_fmas = n + nout;
+    out->sweep_fp64_flops = pairs * (pair_ops + pair_fmas) + rings * 2 * ring_fmas;
+    out->sweep_fp64_ops = pairs * pair_ops + rings * ring_fmas + Qf * kExpFp64Ops;
     out->exps = Qf;
     out->tensor_flops = fp64 ? 0.0 : 3.0 * 2.0 * (n2 - n) * Qf;
     out->newton_flops = 2.0 * mn->gaunt_nnz + n * n * n / 3 + 2 * n * n;
@@ -650,7 +768,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
     // mixed sweeps accumulate moments per list slot; every slot is cleared by its consumer, but an
     // aborted closure could leave partial sums behind
     if (mn->d_Vacc)
-        CUDA_OK(cudaMemsetAsync(mn->d_Vacc, 0, sizeof(double) * (size_t)mn->mesh->C * mn->n2, s));
+        CUDA_OK(cudaMemsetAsync(mn->d_Vacc, 0, sizeof(double) * (size_t)mn->vs * mn->n2, s));
     int rc = launch_begin(mn, T, mn->st, C, u, alpha_in, first, np, s, learned);
     if (rc) return rc;
     if (learned) {

@@ -15,6 +15,10 @@
 #define KITRT_MAX_NMOM 21     // (5+1)(5+2)/2
 #define KITRT_MAX_NMOM2 66    // degree-10 2D basis: (10+1)(10+2)/2
 
+// FP64-pipe instructions of one kexp on its common path (kexp.cuh): 2 for the rounding to the
+// table index, 2 for the two-part reduction, 4 for the polynomial, 1 for the table scaling.
+constexpr int kExpFp64Ops = 9;
+
 // Per-cell Newton phase.
 enum : int32_t { PH_DONE = 0, PH_INIT = 1, PH_NEWTON = 2 };
 
@@ -45,6 +49,12 @@ struct Tables {
     const float *w32;
     const float *wox32, *woy32;  // FP32 copies of w * Omega
     const double *exptab;     // [256] 2^(j/256) for kexp
+    // sum-factorised sweeps (sweep.cuh): rings of P pairs of points; R rings (row R of the ring
+    // tables is zero, for padding pairs); npair = Qf / 2 pairs
+    int R, P, npair;
+    const double *ptrig;      // [Qp/2 x (4N+1)] azimuthal factors of each pair
+    const double *ringP;      // [(R+1) x n2] P_c(mu_r)
+    const double *ringWP;     // [(R+1) x n2] w_r P_c(mu_r)
 };
 
 struct NewtonState {
@@ -104,7 +114,11 @@ struct kitrt_mn {
     double *d_ox = nullptr, *d_oy = nullptr;  // [Qp] folded directions (0 on padding), S_N step
     float *d_ox32 = nullptr, *d_oy32 = nullptr;
     double *d_V = nullptr;               // [C x n2] moments scratch (kitrt_hessian)
-    double *d_Vacc = nullptr;            // [C x n2] mixed sweeps: moment accumulators per list slot
+    double *d_Vacc = nullptr;            // [n2 x vs] sweeps: partial moments per list slot and part
+    int vs = 0;                          // column stride of d_Vacc (C + room for split parts)
+    int target_mixed = 0, target_fp64 = 0, grid_fp64 = 0;  // work items / grid of the sweeps
+    int R = 0, P = 0;                    // rings and pairs per ring of the folded rule
+    double *d_ptrig = nullptr, *d_ringP = nullptr, *d_ringWP = nullptr;
     double *d_exptab = nullptr;          // [256] 2^(j/256)
     void *d_mlp16 = nullptr;             // learned closure: BF16 network parameters
     float *d_mlp_norm = nullptr;         // [4 (n-1)] feature and output means / scales
@@ -174,6 +188,7 @@ int launch_mlp_infer(kitrt_mn *mn, const double *u, const int32_t *list, const i
                      double *alpha, cudaStream_t s);
 int launch_learned_pass(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u,
                         float *psi32, int first, cudaStream_t s);
+int fp64_sweep_grid(const kitrt_mn *mn);
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s,
                      bool filter = false, float *psi32 = nullptr, double *Vacc = nullptr);

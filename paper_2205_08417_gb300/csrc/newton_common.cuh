@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include "kitrt_internal.cuh"
+#include "sweep.cuh"
 
 namespace kitrt_dev {
 
@@ -248,13 +249,15 @@ constexpr int kPostBlock = 64;
 template <int NN>
 __global__ void __launch_bounds__(kPostBlock)
 post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
-                   double *__restrict__ Vacc, int vs, int mixed)
+                   double *__restrict__ Vacc, int vs, int mixed, int target_items)
 {
     constexpr int n2 = Dims<NN>::n2;
     __shared__ double sV[n2 * kPostBlock];  // [n2][thread]
     const int32_t *list_in = S.list[k & 1];
     int32_t *list_out = S.list[(k + 1) & 1];
     const int cnt_in = S.cnt[k % 3];
+    // the sweeps split the quadrature of each tile into `parts` column blocks (sweep.cuh)
+    const int parts = sweep_split(cnt_in, target_items, T.Qp / 32).parts;
     int32_t *cnt_out = &S.cnt[(k + 1) % 3];
     const int stride = gridDim.x * blockDim.x;
     const int rounds = (cnt_in + stride - 1) / stride;
@@ -264,14 +267,19 @@ post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k,
         int cell = -1, ev = 0;
         if (it < cnt_in) {
             cell = list_in[it];
-            // the slot's moments are a column of the [n2 x vs] accumulator: consecutive slots
-            // (threads) read and clear consecutive addresses
-            double *row = Vacc + it;
+            // the slot's moments are column `it` of each part's block of the [n2 x vs]
+            // accumulator: consecutive slots (threads) read and clear consecutive addresses; the
+            // parts are added in order
             double *mine = sV + threadIdx.x;
 #pragma unroll
-            for (int c = 0; c < n2; ++c) mine[c * kPostBlock] = row[(size_t)c * vs];
+            for (int c = 0; c < n2; ++c) mine[c * kPostBlock] = 0.0;
+            for (int p = 0; p < parts; ++p) {
+                double *row = Vacc + (size_t)p * cnt_in + it;
 #pragma unroll
-            for (int c = 0; c < n2; ++c) row[(size_t)c * vs] = 0.0;
+                for (int c = 0; c < n2; ++c) mine[c * kPostBlock] += row[(size_t)c * vs];
+#pragma unroll
+                for (int c = 0; c < n2; ++c) row[(size_t)c * vs] = 0.0;
+            }
             if constexpr (NN <= 3)
                 cont = newton_post_thread<NN>(T, S, np, cell, mine, kPostBlock, u, mixed != 0, ev);
             else

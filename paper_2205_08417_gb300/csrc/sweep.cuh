@@ -1,0 +1,126 @@
+// Sum-factorised quadrature sums of the closure's dual on the folded product rule
+// [Sec. 3.2, Eq. spherical-coordinatesProduct: Gauss-Legendre points in mu times equally spaced
+// azimuths; Sec. 3.1: real spherical harmonics m_c = N_l^|k| P_l^|k|(mu) T_k(phi)].
+//
+// On a ring (one |mu|) every basis function is a Legendre factor times an azimuthal factor
+// T_k(phi) (1, sqrt2 cos(k phi) or sqrt2 sin(|k| phi)), so
+//   exponent   z(mu_r, phi) = alpha . m = sum_{k=-N..N} A_k(r) T_k(phi),
+//              A_k(r) = sum_{c: k(c) = k} alpha_c P_c(mu_r)                 (once per ring),
+//   moments    V_c = sum_r w_r P_c(mu_r) B_k(c)(r),  B_k(r) = sum_phi e(mu_r, phi) T_k(phi).
+// The azimuths of a ring come in pairs (phi, 2 pi - phi) whose cosines agree and whose sines are
+// opposite, so with C = sum_{k>=0} A_k T_k and S = sum_{k<0} A_k T_k at the pair's first point,
+//   z = C + S and z' = C - S,   B_k += (e + e') T_k (k >= 0),   B_k += (e - e') T_k (k < 0).
+// A pass over a cell's Q' points then costs about (2N+3)/2 FP64 operations per point for the
+// exponent and (2L+3)/2 for moments up to degree L, instead of n and nmom(L) per point, plus n and
+// nmom(L) per ring. The ring's remaining pair, (0, pi), has no sine terms and is summed directly.
+//
+// Tables (built by kitrt_mn_init in this point order): pair p covers folded points 2p and 2p+1;
+// ring of pair p = p / P for p < npair (P pairs per ring), the all-zero row R for padding pairs;
+// pair 0 of each ring is the (0, pi) pair. ptrig [npair_padded x (4N+1)]: T_0..T_2N at the pair's
+// first point (cosines), then sqrt2 sin(k phi), k = 1..2N (for the (0, pi) pair: T_k(pi)).
+// ringP, ringWP [(R+1) x n2]: P_c(mu_r) and w_r P_c(mu_r) over the degree-2N basis.
+#pragma once
+
+#include "kexp.cuh"
+#include "kitrt_internal.cuh"
+
+namespace kitrt_dev {
+
+// Position of azimuthal index k in a coefficient vector of degree L: k >= 0 at k, k < 0 at L+|k|.
+__host__ __device__ constexpr int kslot(int L, int k) { return k >= 0 ? k : L - k; }
+// Index of basis function (l, k), l + |k| even, in the order l ascending, then k ascending.
+__host__ __device__ constexpr int cindex(int l, int k) { return l * (l + 1) / 2 + (k + l) / 2; }
+
+// Exponent coefficients A_k of one ring from the trial alpha (degree NN).
+template <int NN>
+__device__ __forceinline__ void ring_coeffs(const double (&at)[(NN + 1) * (NN + 2) / 2],
+                                            const double *__restrict__ Pr, double (&A)[2 * NN + 1])
+{
+#pragma unroll
+    for (int j = 0; j < 2 * NN + 1; ++j) A[j] = 0.0;
+#pragma unroll
+    for (int l = 0; l <= NN; ++l)
+#pragma unroll
+        for (int k = -l; k <= l; k += 2) {
+            const int c = cindex(l, k);
+            A[kslot(NN, k)] = fma(at[c], __ldg(Pr + c), A[kslot(NN, k)]);
+        }
+}
+
+// Moments of the finished ring: V_c += w_r P_c(mu_r) B_k(c), c over the degree-LB basis; the
+// azimuthal sums are cleared for the next ring.
+template <int LB, typename Acc>
+__device__ __forceinline__ void ring_flush(const double *__restrict__ wPr, double (&B)[2 * LB + 1],
+                                           Acc &&V)
+{
+#pragma unroll
+    for (int l = 0; l <= LB; ++l)
+#pragma unroll
+        for (int k = -l; k <= l; k += 2) {
+            const int c = cindex(l, k);
+            double &v = V(c);
+            v = fma(__ldg(wPr + c), B[kslot(LB, k)], v);
+        }
+#pragma unroll
+    for (int j = 0; j < 2 * LB + 1; ++j) B[j] = 0.0;
+}
+
+// One pair of points: both exponentials (e1 at the pair's first point, e2 at its mirror, or at
+// phi = 0 and phi = pi for the ring's (0, pi) pair) and their azimuthal sums up to degree LB.
+// t is the pair's row of ptrig (row width 4 NN + 1).
+template <int NN, int LB>
+__device__ __forceinline__ void pair_eval(const double (&A)[2 * NN + 1], const double *__restrict__ t,
+                                          bool zero_pi, const double *__restrict__ exptab,
+                                          double (&B)[2 * LB + 1], double &e1, double &e2)
+{
+    constexpr int L2 = 2 * NN;  // sines of the row start at t[L2 + 1]
+    if (!zero_pi) {
+        double c = A[0];  // T_0 = 1
+#pragma unroll
+        for (int k = 1; k <= NN; ++k) c = fma(A[k], __ldg(t + k), c);
+        double s = A[NN + 1] * __ldg(t + L2 + 1);
+#pragma unroll
+        for (int k = 2; k <= NN; ++k) s = fma(A[NN + k], __ldg(t + L2 + k), s);
+        e1 = kexp(c + s, exptab);
+        e2 = kexp(c - s, exptab);
+        const double ep = e1 + e2, em = e1 - e2;
+        B[0] += ep;
+#pragma unroll
+        for (int k = 1; k <= LB; ++k) B[k] = fma(ep, __ldg(t + k), B[k]);
+#pragma unroll
+        for (int k = 1; k <= LB; ++k) B[LB + k] = fma(em, __ldg(t + L2 + k), B[LB + k]);
+    } else {
+        double z1 = A[0], z2 = A[0];
+#pragma unroll
+        for (int k = 1; k <= NN; ++k) {
+            z1 = fma(A[k], __ldg(t + k), z1);
+            z2 = fma(A[k], __ldg(t + L2 + k), z2);
+        }
+        e1 = kexp(z1, exptab);
+        e2 = kexp(z2, exptab);
+        B[0] += e1 + e2;
+#pragma unroll
+        for (int k = 1; k <= LB; ++k) B[k] = fma(e1, __ldg(t + k), fma(e2, __ldg(t + L2 + k), B[k]));
+    }
+}
+
+// Split of a sweep's work: tiles of 128 listed cells times parts of the quadrature (units of 16
+// pairs). When few cells are listed each tile's quadrature is split over up to `nunits` parts so
+// that every SM gets work; part j of list slot i lands in column j * cnt + i of the accumulator,
+// and the Newton kernel adds the parts in order (deterministic). The same function sizes the
+// split in the sweep and in its consumer.
+struct SweepSplit {
+    int tiles, parts, units_per_part;
+};
+__host__ __device__ inline SweepSplit sweep_split(int cnt, int target_items, int nunits)
+{
+    SweepSplit sp;
+    sp.tiles = (cnt + 127) / 128;
+    int ks = sp.tiles > 0 && target_items > 0 ? (target_items + sp.tiles - 1) / sp.tiles : 1;
+    ks = ks < 1 ? 1 : (ks > nunits ? nunits : ks);
+    sp.units_per_part = (nunits + ks - 1) / ks;
+    sp.parts = (nunits + sp.units_per_part - 1) / sp.units_per_part;
+    return sp;
+}
+
+}  // namespace kitrt_dev
