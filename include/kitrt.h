@@ -155,11 +155,12 @@ int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_
  *                      moments run on tensor cores; L = 2N in FP64 mode), per ring the exponent
  *                      coefficients (n FMA) and the moments (nmom(L) FMA);
  *   sweep_fp64_ops     FP64-pipe instructions of the same sweep including the exponentials
- *                      (9 per exp on the common path of the table-driven method);
+ *                      (8 per exp on the common path of the table-driven method);
  *   exps               exponentials per evaluation (Q');
  *   tensor_flops       mixed modes: 3 x 2 (n2 - n) Q' on tensor cores (three split products);
  *   newton_flops       the per-cell Newton step: 2 nnz (Hessian) + n^3/3 + 2n^2 (Cholesky,
- *                      solves). */
+ *                      solves);
+ *   sweep_grid, sweep_items  launch shape of the sweep on this device. */
 typedef struct {
     int32_t nmom, nmom2, nquad_folded, gaunt_nnz;
     double sweep_fp64_flops;
@@ -167,6 +168,8 @@ typedef struct {
     double tensor_flops;
     double newton_flops;
     double sweep_fp64_ops;
+    int32_t sweep_grid;     /* CTAs of the mode's quadrature sweep (persistent grid) */
+    int32_t sweep_items;    /* work items (cell tiles x quadrature parts) it aims at per launch */
 } kitrt_work;
 int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out);
 

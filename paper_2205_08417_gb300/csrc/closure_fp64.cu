@@ -574,18 +574,15 @@ int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
 // Grid of the FP64 sweep: as many CTAs as are resident on all SMs at once.
 int fp64_sweep_grid(const kitrt_mn *mn)
 {
-    int resident = 0;
-    cudaError_t e = cudaErrorInvalidValue;
+    int resident = 1;
     switch (mn->N) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<1>, kSweepThreads, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<2>, kSweepThreads, 0); break;
-    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<3>, kSweepThreads, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<4>, kSweepThreads, 0); break;
-    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, sweep64_kernel<5>, kSweepThreads, 0); break;
+    case 1: resident = resident_ctas(sweep64_kernel<1>, kSweepThreads, 0, 8); break;
+    case 2: resident = resident_ctas(sweep64_kernel<2>, kSweepThreads, 0, 8); break;
+    case 3: resident = resident_ctas(sweep64_kernel<3>, kSweepThreads, 0, 8); break;
+    case 4: resident = resident_ctas(sweep64_kernel<4>, kSweepThreads, 0, 8); break;
+    case 5: resident = resident_ctas(sweep64_kernel<5>, kSweepThreads, 0, 8); break;
     default: break;
     }
-    if (e != cudaSuccess || resident < 1) resident = 1;
-    if (resident > 8) resident = 8;
     return mn->nsm * resident;
 }
 

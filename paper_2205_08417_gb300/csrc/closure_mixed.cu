@@ -180,10 +180,8 @@ struct MixedSmem {
     static __host__ __device__ constexpr int off_Bhi(int b) { return b * buf_bytes + 2 * A_bytes; }
     static __host__ __device__ constexpr int off_Blo(int b) { return b * buf_bytes + 2 * A_bytes + B_bytes; }
     static constexpr int off_V = (2 * buf_bytes + 1023) / 1024 * 1024;
-    static constexpr int V_bytes = kTileM * Dims<NN>::n2 * 8;
-    static constexpr int off_H = off_V + V_bytes;
-    static constexpr int H_bytes = kWarpsM * Dims<NN>::n * Dims<NN>::n * 8;
-    static constexpr int off_bar = off_H + H_bytes;
+    static constexpr int V_bytes = kTileM * Dims<NN>::n * 8;      // second half's gradient sums
+    static constexpr int off_bar = off_V + V_bytes;
     static constexpr int total = off_bar + 64;
     static constexpr int kmma = BF16 ? 16 : 8;                   // MMA K
     // byte offset of element (row r, k) inside an operand chunk
@@ -193,6 +191,25 @@ struct MixedSmem {
     }
 };
 
+// E rounded to the tensor-core input format, split into a high and a low part, at (row r, k) of
+// the chunk's operand tiles.
+template <bool BF16, typename L>
+__device__ __forceinline__ void store_operand(unsigned char *Ahi, unsigned char *Alo, int r, int kk, float e)
+{
+    if (BF16) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(e);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(e - __bfloat162float(hi));
+        *(__nv_bfloat16 *)(Ahi + L::elem_off(r, kk)) = hi;
+        *(__nv_bfloat16 *)(Alo + L::elem_off(r, kk)) = lo;
+    } else {
+        uint32_t hi, lo;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(e));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(e - __uint_as_float(hi)));
+        *(uint32_t *)(Ahi + L::elem_off(r, kk)) = hi;
+        *(uint32_t *)(Alo + L::elem_off(r, kk)) = lo;
+    }
+}
+
 // Work item = (tile of 128 listed cells, range of quadrature chunks). When few cells are listed
 // (the later sweeps of a closure), each tile's quadrature range is split over several CTAs
 // (sweep_split) so that every SM gets work; each work item stores its partial moments with plain
@@ -200,7 +217,7 @@ struct MixedSmem {
 // Vacc[c vs_c + (p cnt + j) vs_s]; [n2 x vs] columns for the Newton sweeps, [C x n2] rows and one
 // part for the moments of given alphas), and the Newton kernel adds the parts in order.
 template <int NN, bool BF16, bool MOMENTS_ONLY>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, NN <= 3 ? 2 : 1)
 eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                   const double *__restrict__ alpha_in, double *__restrict__ Vacc, int vs_c, int vs_s,
                   int C, int target_items, float *__restrict__ psi32)
@@ -302,31 +319,19 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                     ring_coeffs<NN>(at, T.ringP + (size_t)rg * n2, A);
                     ring = rg;
                 }
-                double e1 = 0.0, e2 = 0.0;
+                float f1 = 0.0f, f2 = 0.0f;
                 if (active) {
+                    double e1, e2;
                     pair_eval<NN, NN>(A, T.ptrig + (size_t)pr * TW, pr < T.npair && pr % T.P == 0,
                                       T.exptab, B, e1, e2);
+                    f1 = exp_to_float(e1);
+                    f2 = exp_to_float(e2);
                     // ansatz of the trial point (the last accepted trial leaves the solution's)
-                    if (psi32)
-                        *(float2 *)(psi32 + (size_t)cell * Qp + 2 * pr) = make_float2((float)e1, (float)e2);
+                    if (psi32) *(float2 *)(psi32 + (size_t)cell * Qp + 2 * pr) = make_float2(f1, f2);
                 }
                 const int kk = h * (kChunk / 2) + 2 * i;
-                const float ef[2] = {(float)e1, (float)e2};
-#pragma unroll
-                for (int o = 0; o < 2; ++o) {
-                    if (BF16) {
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(ef[o]);
-                        const __nv_bfloat16 lo = __float2bfloat16_rn(ef[o] - __bfloat162float(hi));
-                        *(__nv_bfloat16 *)(Ahi + L::elem_off(r, kk + o)) = hi;
-                        *(__nv_bfloat16 *)(Alo + L::elem_off(r, kk + o)) = lo;
-                    } else {
-                        uint32_t hi, lo;
-                        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(ef[o]));
-                        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(ef[o] - __uint_as_float(hi)));
-                        *(uint32_t *)(Ahi + L::elem_off(r, kk + o)) = hi;
-                        *(uint32_t *)(Alo + L::elem_off(r, kk + o)) = lo;
-                    }
-                }
+                store_operand<BF16, L>(Ahi, Alo, r, kk, f1);
+                store_operand<BF16, L>(Ahi, Alo, r, kk + 1, f2);
             }
             // stage the chunk of the split table (row-major [2][NP x Qp] in global: high part,
             // then low part), in 16-byte pieces
@@ -426,15 +431,24 @@ int launch_mixed_impl(kitrt_mn *mn, const Tables &T, const NewtonState &S, const
 {
     using L = MixedSmem<NN, BF16>;
     if (ensure_dyn_smem(eval_mixed_kernel<NN, BF16, MO>, L::total)) return KITRT_ECUDA;
-    // persistent grid of one CTA per SM; aim at two work items per CTA (the moments of given
-    // alphas take one part per tile: rows of Vout are written whole)
-    eval_mixed_kernel<NN, BF16, MO><<<mn->nsm, kThreads, L::total, s>>>(
+    // persistent grid of the CTAs that fit on the SMs at once; the work is split into about four
+    // items per CTA (the moments of given alphas take one part per tile: rows of Vout are written
+    // whole)
+    eval_mixed_kernel<NN, BF16, MO><<<mn->grid_mixed, kThreads, L::total, s>>>(
         T, S, k, BF16 ? (const void *)mn->d_Mhi16 : (const void *)mn->d_Mhi32, alpha_in, Vacc,
         MO ? 1 : mn->vs, MO ? Dims<NN>::n2 : 1, C, MO ? 0 : mn->target_mixed, psi32);
     if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
     (void)u;
     (void)np;
     return KITRT_OK;
+}
+
+template <int NN, bool BF16>
+int mixed_grid_impl(const kitrt_mn *mn)
+{
+    using L = MixedSmem<NN, BF16>;
+    if (ensure_dyn_smem(eval_mixed_kernel<NN, BF16, false>, L::total)) return mn->nsm;
+    return mn->nsm * resident_ctas(eval_mixed_kernel<NN, BF16, false>, kThreads, L::total, 2);
 }
 
 template <bool MO>
@@ -458,6 +472,19 @@ int launch_mixed_dispatch(kitrt_mn *mn, const Tables &T, const NewtonState &S, c
 }
 
 }  // namespace
+
+// Grid of the tensor-core sweep of a solver (CTAs resident at once).
+int mixed_sweep_grid(const kitrt_mn *mn)
+{
+    const bool bf16 = mn->p.mode == KITRT_MIXED_BF16;
+    switch (mn->N) {
+    case 1: return bf16 ? mixed_grid_impl<1, true>(mn) : mixed_grid_impl<1, false>(mn);
+    case 2: return bf16 ? mixed_grid_impl<2, true>(mn) : mixed_grid_impl<2, false>(mn);
+    case 3: return bf16 ? mixed_grid_impl<3, true>(mn) : mixed_grid_impl<3, false>(mn);
+    case 4: return bf16 ? mixed_grid_impl<4, true>(mn) : mixed_grid_impl<4, false>(mn);
+    default: return bf16 ? mixed_grid_impl<5, true>(mn) : mixed_grid_impl<5, false>(mn);
+    }
+}
 
 int launch_eval_mixed(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u, int k,
                       NewtonParams np, cudaStream_t s, float *psi32)

@@ -18,7 +18,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 8;
-constexpr int kBatch = 4;  // cells per warp batch in the FP32 flux
+constexpr int kBatch = 4;     // cells per warp batch in the FP32 flux
+constexpr int kTogether = 2;  // cells of a batch whose points one pass over the tables serves
 
 template <int NN, typename PsiT>
 __global__ void __launch_bounds__(kWarps * 32)
@@ -140,71 +141,103 @@ __device__ __forceinline__ int warp_reduce_scatter(const float (&F)[n], const fl
     return (lane & ((1 << (5 - H)) - 1)) == 0 ? lane >> (5 - H) : -1;
 }
 
+// The FP32 flux of the mixed modes. FP64 instructions are rare on this GPU (2 per clock per SM), so
+// none is spent on warp-uniform values: normals and inverse areas come from the mesh's FP32
+// copies, the per-cell coefficients are converted by different lanes at once, and the update
+// increment dt (-F/A + R(u)) is formed in FP32; only u += increment is FP64 (lanes over the
+// (cell, moment) elements of a batch). Each lane sums its ~Q'/32 points in plain FP32; the warp
+// reduction of the 32 lane sums is compensated.
 template <int NN>
 __global__ void __launch_bounds__(kWarps * 32)
-flux_update32_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restrict__ nrm,
-                     const double *__restrict__ area, const float *__restrict__ psi,
+flux_update32_kernel(Tables T, const int4 *__restrict__ nbr, const float *__restrict__ nrm32,
+                     const float *__restrict__ inva32, const float *__restrict__ psi,
                      double *__restrict__ u, const double *__restrict__ sa,
-                     const double *__restrict__ ss, const double *__restrict__ qs, double dt,
+                     const double *__restrict__ ss, const double *__restrict__ qs, float dt,
                      int bc, int C)
 {
     constexpr int n = (NN + 1) * (NN + 2) / 2;
-    __shared__ double sF[kWarps][kBatch * n];
+    __shared__ float sF[kWarps][kBatch * n];
+    __shared__ float sK[kWarps][kBatch][4];  // per cell: sigma_a, sigma_s, q, 1/A (FP32)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int Qp = T.Qp;
     for (int base = (blockIdx.x * kWarps + wib) * kBatch; base < C; base += gridDim.x * kWarps * kBatch) {
         const int nb_cells = C - base < kBatch ? C - base : kBatch;
-        for (int ci = 0; ci < nb_cells; ++ci) {
-            const int i = base + ci;
-            const int4 nb = nbr[i];
-            const float nx0 = (float)nrm[6 * (size_t)i], ny0 = (float)nrm[6 * (size_t)i + 1];
-            const float nx1 = (float)nrm[6 * (size_t)i + 2], ny1 = (float)nrm[6 * (size_t)i + 3];
-            const float nx2 = (float)nrm[6 * (size_t)i + 4], ny2 = (float)nrm[6 * (size_t)i + 5];
-            const float *pi_row = psi + (size_t)i * Qp;
-            // upwind rows: the neighbour's row, or the cell's own row as the Neumann ghost (its
-            // fluctuation is then zero) scaled by 0 for the vacuum ghost; loads are issued
-            // unconditionally so that all four rows of a point are in flight together
-            const float *r0 = nb.x >= 0 ? psi + (size_t)nb.x * Qp : pi_row;
-            const float *r1 = nb.y >= 0 ? psi + (size_t)nb.y * Qp : pi_row;
-            const float *r2 = nb.z >= 0 ? psi + (size_t)nb.z * Qp : pi_row;
-            const float g0 = (nb.x >= 0 || bc == 0) ? 1.0f : 0.0f;
-            const float g1 = (nb.y >= 0 || bc == 0) ? 1.0f : 0.0f;
-            const float g2 = (nb.z >= 0 || bc == 0) ? 1.0f : 0.0f;
-            float F[n], Fc[n];
+        if (lane < 4 * nb_cells) {
+            const int ci = lane >> 2, which = lane & 3, i = base + ci;
+            const double v = which == 0 ? sa[i] : which == 1 ? ss[i] : qs[i];
+            sK[wib][ci][which] = which == 3 ? inva32[i] : (float)v;
+        }
+        // kTogether cells at a time share each point's table loads (directions, weights, basis)
+        for (int c0 = 0; c0 < nb_cells; c0 += kTogether) {
+            int4 nb[kTogether];
+            float nx[kTogether][3], ny[kTogether][3], g[kTogether][3];
+            const float *own[kTogether], *up[kTogether][3];
 #pragma unroll
-            for (int a = 0; a < n; ++a) F[a] = Fc[a] = 0.0f;
-#pragma unroll 2
-            for (int q = lane; q < Qp; q += 32) {
-                const float pi = __ldg(pi_row + q);
-                const float p0 = __ldg(r0 + q), p1 = __ldg(r1 + q), p2 = __ldg(r2 + q);
-                const float wx = T.wox32[q], wy = T.woy32[q];
-                const float d0 = fmaf(wx, nx0, wy * ny0);
-                const float d1 = fmaf(wx, nx1, wy * ny1);
-                const float d2 = fmaf(wx, nx2, wy * ny2);
-                float s = 0.0f;
-                s = fmaf(fminf(d0, 0.0f), fmaf(g0, p0, -pi), s);
-                s = fmaf(fminf(d1, 0.0f), fmaf(g1, p1, -pi), s);
-                s = fmaf(fminf(d2, 0.0f), fmaf(g2, p2, -pi), s);
+            for (int t = 0; t < kTogether; ++t) {
+                // a missing partner cell repeats the last real one; its sums are not stored
+                const int i = base + min(c0 + t, nb_cells - 1);
+                nb[t] = nbr[i];
 #pragma unroll
-                for (int a = 0; a < n; ++a) {
-                    const float y = fmaf(T.Mt32[a * Qp + q], s, -Fc[a]);
-                    const float t = F[a] + y;
-                    Fc[a] = (t - F[a]) - y;
-                    F[a] = t;
+                for (int f = 0; f < 3; ++f) {
+                    nx[t][f] = nrm32[6 * (size_t)i + 2 * f];
+                    ny[t][f] = nrm32[6 * (size_t)i + 2 * f + 1];
+                }
+                own[t] = psi + (size_t)i * Qp;
+                // upwind rows: the neighbour's row, or the cell's own row as the Neumann ghost
+                // (its fluctuation is then zero) scaled by 0 for the vacuum ghost; loads are
+                // issued unconditionally so that all rows of a point are in flight together
+                const int nbf[3] = {nb[t].x, nb[t].y, nb[t].z};
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    up[t][f] = nbf[f] >= 0 ? psi + (size_t)nbf[f] * Qp : own[t];
+                    g[t][f] = (nbf[f] >= 0 || bc == 0) ? 1.0f : 0.0f;
                 }
             }
-            // value = F - Fc per lane; compensated reduce-scatter keeps the rounding errors
-            float rs, re;
-            const int slot = warp_reduce_scatter<n>(F, Fc, lane, rs, re);
-            if (slot >= 0 && slot < n) sF[wib][ci * n + slot] = (double)rs + (double)re;
+            float F[kTogether][n], Fc[n];
+#pragma unroll
+            for (int a = 0; a < n; ++a) Fc[a] = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kTogether; ++t)
+#pragma unroll
+                for (int a = 0; a < n; ++a) F[t][a] = 0.0f;
+#pragma unroll 2
+            for (int q = lane; q < Qp; q += 32) {
+                const float wx = T.wox32[q], wy = T.woy32[q];
+                float Mq[n];
+#pragma unroll
+                for (int a = 0; a < n; ++a) Mq[a] = T.Mt32[a * Qp + q];
+#pragma unroll
+                for (int t = 0; t < kTogether; ++t) {
+                    const float pi = __ldg(own[t] + q);
+                    float s = 0.0f;
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        const float d = fmaf(wx, nx[t][f], wy * ny[t][f]);
+                        s = fmaf(fminf(d, 0.0f), fmaf(g[t][f], __ldg(up[t][f] + q), -pi), s);
+                    }
+#pragma unroll
+                    for (int a = 0; a < n; ++a) F[t][a] = fmaf(Mq[a], s, F[t][a]);
+                }
+            }
+            // compensated reduce-scatter of the 32 lane sums of each cell
+#pragma unroll
+            for (int t = 0; t < kTogether; ++t) {
+                float rs, re;
+                const int slot = warp_reduce_scatter<n>(F[t], Fc, lane, rs, re);
+                if (c0 + t < nb_cells && slot >= 0 && slot < n) sF[wib][(c0 + t) * n + slot] = rs + re;
+            }
         }
         __syncwarp();
         for (int idx = lane; idx < nb_cells * n; idx += 32) {
             const int ci = idx / n, a = idx - ci * n, i = base + ci;
             const double ua = u[(size_t)i * n + a];
-            const double u0 = u[(size_t)i * n];
-            const double R = -sa[i] * ua - ss[i] * (ua - (a == 0 ? u0 : 0.0)) + qs[i] * T.mbar[a];
-            u[(size_t)i * n + a] = ua - dt / area[i] * sF[wib][idx] + dt * R;
+            const float* k = sK[wib][ci];
+            // R = -sigma_a u - sigma_s (u - u_0 e_0) + q <m>: the scattering term of moment 0
+            // cancels exactly
+            const float sig = a == 0 ? k[0] : k[0] + k[1];
+            const float R = fmaf(-sig, (float)ua, k[2] * T.mbar32[a]);
+            const float inc = dt * fmaf(-k[3], sF[wib][idx], R);
+            u[(size_t)i * n + a] = ua + (double)inc;
         }
         __syncwarp();
     }
@@ -241,7 +274,7 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
                 T, m->d_nbr, m->d_nrm, m->d_area, psi, u, sa, ss, q, dt, bc, C);               \
         else                                                                                   \
             flux_update32_kernel<NN><<<grid32, kWarps * 32, 0, s>>>(                            \
-                T, m->d_nbr, m->d_nrm, m->d_area, psi32, u, sa, ss, q, dt, bc, C);             \
+                T, m->d_nbr, m->d_nrm32, m->d_inva32, psi32, u, sa, ss, q, (float)dt, bc, C);  \
         break;
     switch (mn->N) {
         FLUX_CASE(1)

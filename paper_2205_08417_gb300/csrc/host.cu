@@ -244,6 +244,7 @@ Tables kitrt_mn::tables() const
     T.w32 = d_w32;
     T.wox32 = d_wox32;
     T.woy32 = d_woy32;
+    T.mbar32 = d_mbar32;
     T.exptab = d_exptab;
     T.R = R;
     T.P = P;
@@ -363,11 +364,20 @@ int32_t kitrt_mesh_create(const double *xy, int32_t nverts, const int32_t *tri, 
     for (int32_t c = 0; c < ntri; ++c)
         nb4[c] = make_int4(m->nbr[3 * c], m->nbr[3 * c + 1], m->nbr[3 * c + 2], 0);
     std::vector<double> hpa(ntri);
-    for (int32_t c = 0; c < ntri; ++c) hpa[c] = m->perim[c] / (2.0 * m->area[c]);
+    std::vector<float> nrm32(6 * (size_t)ntri), inva32(ntri);
+    for (int32_t c = 0; c < ntri; ++c) {
+        hpa[c] = m->perim[c] / (2.0 * m->area[c]);
+        inva32[c] = (float)(1.0 / m->area[c]);
+        for (int k = 0; k < 6; ++k) nrm32[6 * (size_t)c + k] = (float)m->nrm[6 * (size_t)c + k];
+    }
     bool ok = cudaMalloc(&m->d_nbr, sizeof(int4) * ntri) == cudaSuccess &&
               cudaMalloc(&m->d_nrm, sizeof(double) * 6 * ntri) == cudaSuccess &&
               cudaMalloc(&m->d_area, sizeof(double) * ntri) == cudaSuccess &&
-              cudaMalloc(&m->d_hpa, sizeof(double) * ntri) == cudaSuccess;
+              cudaMalloc(&m->d_hpa, sizeof(double) * ntri) == cudaSuccess &&
+              cudaMalloc(&m->d_nrm32, sizeof(float) * 6 * ntri) == cudaSuccess &&
+              cudaMalloc(&m->d_inva32, sizeof(float) * ntri) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_nrm32, nrm32.data(), sizeof(float) * 6 * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_inva32, inva32.data(), sizeof(float) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_hpa, hpa.data(), sizeof(double) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_nbr, nb4.data(), sizeof(int4) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_nrm, m->nrm.data(), sizeof(double) * 6 * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -387,6 +397,8 @@ int32_t kitrt_mesh_destroy(kitrt_mesh *m)
     cudaFree(m->d_nrm);
     cudaFree(m->d_area);
     cudaFree(m->d_hpa);
+    cudaFree(m->d_nrm32);
+    cudaFree(m->d_inva32);
     delete m;
     return KITRT_OK;
 }
@@ -557,6 +569,7 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_upload(mn, &mn->d_wox, wox));
     TRY(dev_upload(mn, &mn->d_woy, woy));
     TRY(dev_upload(mn, &mn->d_mbar, mb));
+    TRY(dev_upload(mn, &mn->d_mbar32, std::vector<float>(mb.begin(), mb.end())));
     TRY(dev_upload(mn, &mn->d_gstart, gstart));
     TRY(dev_upload(mn, &mn->d_gidx, gidx));
     TRY(dev_upload(mn, &mn->d_gcoef, gcoef));
@@ -575,9 +588,9 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_upload(mn, &mn->d_oy, oyp));
     TRY(dev_upload(mn, &mn->d_ox32, oxp32));
     TRY(dev_upload(mn, &mn->d_oy32, oyp32));
-    // 2^(j/256), j = 0..255, rounded to double from extended precision
-    std::vector<double> exptab(256);
-    for (int j = 0; j < 256; ++j) exptab[j] = (double)exp2l((long double)j / 256.0L);
+    // 2^(j/2048), j = 0..2047, rounded to double from extended precision
+    std::vector<double> exptab(2048);
+    for (int j = 0; j < 2048; ++j) exptab[j] = (double)exp2l((long double)j / 2048.0L);
     TRY(dev_upload(mn, &mn->d_exptab, exptab));
     // sum-factorised sweeps: azimuthal factors per pair and Legendre factors per ring
     {
@@ -640,12 +653,14 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
         return KITRT_ECUDA;
     }
     TRY(dev_alloc(mn, &mn->d_psi, C * Qp));
-    // sweep work split (sweep.cuh): the tensor-core sweep runs one CTA per SM and aims at two
-    // work items per CTA; the FP64 sweep fills the SMs with resident CTAs. A split never needs
-    // more than C + target * 128 columns per moment.
-    mn->target_mixed = 2 * mn->nsm;
+    // sweep work split (sweep.cuh): both sweeps run persistent grids of the CTAs that fit on the
+    // SMs at once and split the quadrature of each tile so that every CTA gets several work items
+    // (4 for the tensor-core sweep, 2 for the FP64 sweep). A split never needs more than
+    // C + target * 128 columns per moment.
+    mn->grid_mixed = p.mode == KITRT_FP64 ? mn->nsm : mixed_sweep_grid(mn);
+    mn->target_mixed = 4 * mn->grid_mixed;
     mn->grid_fp64 = fp64_sweep_grid(mn);
-    mn->target_fp64 = mn->grid_fp64;
+    mn->target_fp64 = 2 * mn->grid_fp64;
     mn->vs = (int)C + 128 * std::max(mn->target_mixed, mn->target_fp64) + 128;
     TRY(dev_alloc(mn, &mn->d_Vacc, (size_t)mn->vs * n2));
     if (cudaMemset(mn->d_Vacc, 0, sizeof(double) * (size_t)mn->vs * n2) != cudaSuccess) {
@@ -719,6 +734,8 @@ int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out)
     out->exps = Qf;
     out->tensor_flops = fp64 ? 0.0 : 3.0 * 2.0 * (n2 - n) * Qf;
     out->newton_flops = 2.0 * mn->gaunt_nnz + n * n * n / 3 + 2 * n * n;
+    out->sweep_grid = fp64 ? mn->grid_fp64 : mn->grid_mixed;
+    out->sweep_items = fp64 ? mn->target_fp64 : mn->target_mixed;
     return KITRT_OK;
 }
 

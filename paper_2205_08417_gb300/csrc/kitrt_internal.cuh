@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -16,8 +17,8 @@
 #define KITRT_MAX_NMOM2 66    // degree-10 2D basis: (10+1)(10+2)/2
 
 // FP64-pipe instructions of one kexp on its common path (kexp.cuh): 2 for the rounding to the
-// table index, 2 for the two-part reduction, 4 for the polynomial, 1 for the table scaling.
-constexpr int kExpFp64Ops = 9;
+// table index, 2 for the two-part reduction, 3 for the polynomial, 1 for the table scaling.
+constexpr int kExpFp64Ops = 8;
 
 // Per-cell Newton phase.
 enum : int32_t { PH_DONE = 0, PH_INIT = 1, PH_NEWTON = 2 };
@@ -32,6 +33,8 @@ struct kitrt_mesh {
     double *d_nrm = nullptr;   // [C x 6] scaled outward normals (nx0, ny0, nx1, ny1, nx2, ny2)
     double *d_area = nullptr;  // [C]
     double *d_hpa = nullptr;   // [C] P_i / (2 A_i): largest outflow rate of the cell per unit speed
+    float *d_nrm32 = nullptr;  // [C x 6] FP32 copy of the scaled normals (FP32 flux)
+    float *d_inva32 = nullptr; // [C] FP32 1 / A_i
 };
 
 // Device views handed to kernels by value.
@@ -48,7 +51,8 @@ struct Tables {
     const float *Mt32;        // [n2 x Qp] FP32 copy
     const float *w32;
     const float *wox32, *woy32;  // FP32 copies of w * Omega
-    const double *exptab;     // [256] 2^(j/256) for kexp
+    const float *mbar32;         // [n] FP32 copy of <m>
+    const double *exptab;     // [2048] 2^(j/2048) for kexp
     // sum-factorised sweeps (sweep.cuh): rings of P pairs of points; R rings (row R of the ring
     // tables is zero, for padding pairs); npair = Qf / 2 pairs
     int R, P, npair;
@@ -110,16 +114,17 @@ struct kitrt_mn {
     float *d_Mt32 = nullptr, *d_w32 = nullptr;
     float *d_Mhi32 = nullptr;            // [NP x Qp] TF32-rounded degree-(N+1..2N) basis (mixed)
     unsigned short *d_Mhi16 = nullptr;   // [NP x Qp] BF16 copy
-    float *d_wox32 = nullptr, *d_woy32 = nullptr;
+    float *d_wox32 = nullptr, *d_woy32 = nullptr, *d_mbar32 = nullptr;
     double *d_ox = nullptr, *d_oy = nullptr;  // [Qp] folded directions (0 on padding), S_N step
     float *d_ox32 = nullptr, *d_oy32 = nullptr;
     double *d_V = nullptr;               // [C x n2] moments scratch (kitrt_hessian)
     double *d_Vacc = nullptr;            // [n2 x vs] sweeps: partial moments per list slot and part
     int vs = 0;                          // column stride of d_Vacc (C + room for split parts)
-    int target_mixed = 0, target_fp64 = 0, grid_fp64 = 0;  // work items / grid of the sweeps
+    int target_mixed = 0, target_fp64 = 0;  // work items the sweeps aim at per launch
+    int grid_mixed = 0, grid_fp64 = 0;      // persistent grids of the sweeps
     int R = 0, P = 0;                    // rings and pairs per ring of the folded rule
     double *d_ptrig = nullptr, *d_ringP = nullptr, *d_ringWP = nullptr;
-    double *d_exptab = nullptr;          // [256] 2^(j/256)
+    double *d_exptab = nullptr;          // [2048] 2^(j/2048)
     void *d_mlp16 = nullptr;             // learned closure: BF16 network parameters
     float *d_mlp_norm = nullptr;         // [4 (n-1)] feature and output means / scales
     bool has_mlp = false;
@@ -179,6 +184,31 @@ inline int ensure_dyn_smem(Kern *kernel, size_t smem)
     return KITRT_OK;
 }
 
+// CTAs of a kernel that fit on one SM at once, from its register and shared-memory use and the
+// device's per-SM limits (asks for the largest shared-memory carveout first), at most `cap`.
+template <typename Kern>
+inline int resident_ctas(Kern *kernel, int threads, size_t dyn_smem, int cap)
+{
+    int dev = 0;
+    cudaFuncAttributes fa;
+    int regs_sm = 0, smem_sm = 0, thr_sm = 0, reserved = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, kernel) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return 1;
+    if (cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+        reserved = 1024;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    const int warps = (threads + 31) / 32;
+    const int regs_cta = warps * 32 * ((fa.numRegs + 7) / 8 * 8);  // allocated per warp in 256s
+    int n = thr_sm / threads;
+    if (regs_cta > 0) n = std::min(n, regs_sm / regs_cta);
+    const size_t smem_cta = dyn_smem + fa.sharedSizeBytes + (size_t)reserved;
+    if (smem_cta > 0) n = std::min(n, (int)((size_t)smem_sm / smem_cta));
+    return std::max(1, std::min(n, cap));
+}
+
 // Kernel launchers (closure_fp64.cu, flux.cu).
 int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cudaStream_t s);
 int launch_begin(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
@@ -189,6 +219,7 @@ int launch_mlp_infer(kitrt_mn *mn, const double *u, const int32_t *list, const i
 int launch_learned_pass(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u,
                         float *psi32, int first, cudaStream_t s);
 int fp64_sweep_grid(const kitrt_mn *mn);
+int mixed_sweep_grid(const kitrt_mn *mn);
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s,
                      bool filter = false, float *psi32 = nullptr, double *Vacc = nullptr);

@@ -246,6 +246,10 @@ __device__ __forceinline__ void push_agg(int32_t *list, int32_t *cnt, int cell, 
 // The slot's n2 moments are first copied to shared memory (all loads in flight together), where
 // the Hessian assembly's table-driven reads then find them at shared-memory latency.
 constexpr int kPostBlock = 64;
+// The Newton kernel runs a few times per step on a few thousand cells each, so its code is
+// fetched cold at every launch: the rolled body (factor in local memory, L1-resident) keeps the
+// instruction footprint small.
+constexpr bool kUnrolledNewton = false;
 template <int NN>
 __global__ void __launch_bounds__(kPostBlock)
 post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
@@ -280,7 +284,7 @@ post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k,
 #pragma unroll
                 for (int c = 0; c < n2; ++c) row[(size_t)c * vs] = 0.0;
             }
-            if constexpr (NN <= 3)
+            if constexpr (kUnrolledNewton && NN <= 3)
                 cont = newton_post_thread<NN>(T, S, np, cell, mine, kPostBlock, u, mixed != 0, ev);
             else
                 cont = newton_post_thread_rolled<NN>(T, S, np, cell, mine, kPostBlock, u, mixed != 0, ev);

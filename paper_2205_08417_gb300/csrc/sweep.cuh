@@ -104,6 +104,19 @@ __device__ __forceinline__ void pair_eval(const double (&A)[2 * NN + 1], const d
     }
 }
 
+// An exponential (a non-negative double, or +inf) rounded to float in integer arithmetic, so that
+// the narrow FP64 pipe does not convert it: the exponent is rebiased and the mantissa rounded
+// half away from zero at bit 29 (a carry into the exponent is the correct result); values below
+// the smallest normal float give 0, values beyond the float range give +inf.
+__device__ __forceinline__ float exp_to_float(double e)
+{
+    const long long b = __double_as_longlong(e);
+    const int ex = (int)(b >> 52);  // sign is 0
+    if (ex < 1023 - 126) return 0.0f;
+    const long long f = ((b + (1LL << 28)) >> 29) - ((long long)(1023 - 127) << 23);
+    return f >= (255LL << 23) ? __int_as_float(0x7f800000) : __int_as_float((int)f);
+}
+
 // Split of a sweep's work: tiles of 128 listed cells times parts of the quadrature (units of 16
 // pairs). When few cells are listed each tile's quadrature is split over up to `nunits` parts so
 // that every SM gets work; part j of list slot i lands in column j * cnt + i of the accumulator,

@@ -47,7 +47,8 @@ class Work(C.Structure):
     _fields_ = [("nmom", C.c_int32), ("nmom2", C.c_int32), ("nquad_folded", C.c_int32),
                 ("gaunt_nnz", C.c_int32), ("sweep_fp64_flops", C.c_double), ("exps", C.c_double),
                 ("tensor_flops", C.c_double), ("newton_flops", C.c_double),
-                ("sweep_fp64_ops", C.c_double)]
+                ("sweep_fp64_ops", C.c_double), ("sweep_grid", C.c_int32),
+                ("sweep_items", C.c_int32)]
 
 
 class ProfileEntry(C.Structure):
