@@ -246,9 +246,10 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
     const double *__restrict__ Mt = T.Mt;
     const double *__restrict__ wq = T.w;
 
-    for (int it = blockIdx.x * kWarps + wib; it < cnt_in; it += gridDim.x * kWarps) {
+    // one listed cell: its trial point, the quadrature sums, then (FUSED) the Newton logic or
+    // (otherwise) its moments into column `it` of Vacc
+    auto cell_pass = [&](int it) {
         const int cell = list_in[it];
-        if (FILTER && S.h64[cell] == 0) continue;
         const size_t off = (size_t)cell * n;
         const int ph = S.phase[cell];
         const double ua = lane < n ? u[off + lane] : 0.0;
@@ -281,7 +282,7 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
 #pragma unroll
             for (int c = 0; c < n2; ++c)
                 if (lane == (c & 31)) Vacc[(size_t)c * vs + it] = V[c];
-            continue;
+            return;
         }
         __syncwarp();
 #pragma unroll
@@ -290,6 +291,21 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
         __syncwarp();
         newton_post<NN>(T, S, np, cell, ph, lam, at, ua, Vs, H, list_out, cnt_out, lane, false);
         __syncwarp();
+    };
+    if (FILTER) {
+        // the FP64 companion of the mixed sweep takes only the (rare) cells flagged for an FP64
+        // Hessian: each warp tests 32 list entries at once and evaluates the flagged ones
+        for (int b0 = (blockIdx.x * kWarps + wib) * 32; b0 < cnt_in; b0 += gridDim.x * kWarps * 32) {
+            const int e = b0 + lane;
+            unsigned m = __ballot_sync(kFull, e < cnt_in && S.h64[list_in[e]] != 0);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                cell_pass(b0 + b);
+            }
+        }
+    } else {
+        for (int it = blockIdx.x * kWarps + wib; it < cnt_in; it += gridDim.x * kWarps) cell_pass(it);
     }
 }
 
@@ -399,6 +415,21 @@ finish_kernel(Tables T, NewtonState S, double *__restrict__ alpha_out, double *_
                 psi32[(size_t)cell * Qp + q] = expf(zh) * (1.0f + zl);
             }
         }
+    }
+}
+
+// finish without an ansatz to write (the mixed modes' sweeps already wrote it): the final alpha,
+// element-wise over the C x n entries (coalesced, every lane busy).
+__global__ void finish_alpha_kernel(NewtonState S, double *__restrict__ alpha_out, int polish, int n,
+                                    int C)
+{
+    const size_t total = (size_t)C * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int cell = (int)(e / n);
+        double a = S.alpha[e];
+        if (polish && S.status[cell] == 0) a += S.dir[e];
+        alpha_out[e] = a;
     }
 }
 
@@ -610,6 +641,13 @@ int launch_finish(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
 {
     const int grid = grid_for(mn, C, 8);
     LaunchScope ls(mn, PK_FINISH, s, C);
+    if (!psi && !psi32) {
+        const size_t total = (size_t)C * T.n;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > mn->nsm * 8) blocks = mn->nsm * 8;
+        finish_alpha_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(S, alpha_out, polish, T.n, C);
+        return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
+    }
     KITRT_DISPATCH_N(mn->N, finish_kernel<NN><<<grid, kWarps * 32, 0, s>>>(T, S, alpha_out, psi, psi32, polish, compare_prev, C));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }

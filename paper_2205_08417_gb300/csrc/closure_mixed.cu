@@ -387,7 +387,11 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
         if (*abort_flag) break;
         // partial moments of this work item into its column of the accumulator: the FP64
         // gradient moments of both halves, the tensor-core moments from TMEM (warps 0-3)
+        // A row handed to the FP64 Hessian gets its whole sums in part 0 from the FP64 sweep; its
+        // other parts are stored as zeros, so that every column the Newton kernel reads was
+        // written in this round.
         const bool store = r < rows && (MOMENTS_ONLY || active);
+        const bool zero = !MOMENTS_ONLY && r < rows && cell >= 0 && !active && part > 0;
         double *row = Vacc + ((size_t)part * cnt_in + base + r) * vs_s;
         if (h == 0 && store) {
 #pragma unroll
@@ -404,6 +408,10 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                     for (int i = 0; i < 16; ++i)
                         if (c0 + i < n2 - n) row[(size_t)(n + c0 + i) * vs_c] = (double)v[i];
                 }
+            }
+            if (zero) {
+#pragma unroll
+                for (int c = 0; c < n2; ++c) row[(size_t)c * vs_c] = 0.0;
             }
         }
         tc_fence_before();

@@ -782,10 +782,6 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
     const bool learned = mn->p.mode == KITRT_LEARNED;
     if (learned && !mn->has_mlp) return KITRT_EINVAL;
     CUDA_OK(cudaMemsetAsync(mn->st.cnt, 0, 16 * sizeof(int32_t), s));
-    // mixed sweeps accumulate moments per list slot; every slot is cleared by its consumer, but an
-    // aborted closure could leave partial sums behind
-    if (mn->d_Vacc)
-        CUDA_OK(cudaMemsetAsync(mn->d_Vacc, 0, sizeof(double) * (size_t)mn->vs * mn->n2, s));
     int rc = launch_begin(mn, T, mn->st, C, u, alpha_in, first, np, s, learned);
     if (rc) return rc;
     if (learned) {

@@ -246,10 +246,10 @@ __device__ __forceinline__ void push_agg(int32_t *list, int32_t *cnt, int cell, 
 // The slot's n2 moments are first copied to shared memory (all loads in flight together), where
 // the Hessian assembly's table-driven reads then find them at shared-memory latency.
 constexpr int kPostBlock = 64;
-// The Newton kernel runs a few times per step on a few thousand cells each, so its code is
-// fetched cold at every launch: the rolled body (factor in local memory, L1-resident) keeps the
-// instruction footprint small.
-constexpr bool kUnrolledNewton = false;
+// N <= 3: the fully unrolled body (factor in registers, ~3k instructions per cell); the rolled
+// body (factor in local memory) executes about four times as many instructions and measured
+// slower (0.40 vs 0.30 ms per M_3 step), instruction fetch notwithstanding.
+constexpr bool kUnrolledNewton = true;
 template <int NN>
 __global__ void __launch_bounds__(kPostBlock)
 post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, NewtonParams np,
@@ -272,17 +272,15 @@ post_thread_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k,
         if (it < cnt_in) {
             cell = list_in[it];
             // the slot's moments are column `it` of each part's block of the [n2 x vs]
-            // accumulator: consecutive slots (threads) read and clear consecutive addresses; the
-            // parts are added in order
+            // accumulator (every one written by this round's sweeps): consecutive slots (threads)
+            // read consecutive addresses; the parts are added in order
             double *mine = sV + threadIdx.x;
 #pragma unroll
             for (int c = 0; c < n2; ++c) mine[c * kPostBlock] = 0.0;
             for (int p = 0; p < parts; ++p) {
-                double *row = Vacc + (size_t)p * cnt_in + it;
+                const double *row = Vacc + (size_t)p * cnt_in + it;
 #pragma unroll
                 for (int c = 0; c < n2; ++c) mine[c * kPostBlock] += row[(size_t)c * vs];
-#pragma unroll
-                for (int c = 0; c < n2; ++c) row[(size_t)c * vs] = 0.0;
             }
             if constexpr (kUnrolledNewton && NN <= 3)
                 cont = newton_post_thread<NN>(T, S, np, cell, mine, kPostBlock, u, mixed != 0, ev);
