@@ -73,6 +73,12 @@ def _declare(L):
                               d, i, _dp, _dp, i]
     L.orc_sn_run.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
                              d, i, i, _dp, _dp, i]
+    L.orc_mesh_face_offsets.argtypes = [i, _dp, i, _ip, _dp]
+    L.orc_reconstruct.argtypes = [i, i, _ip, _dp, _dp, _dp, _dp, i, _dp, _dp, _dp]
+    L.orc_flux_update2.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp,
+                                   _dp, d, i, _dp, _dp]
+    L.orc_mn_run2.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
+                              d, i, i, d, i, i, i, _dp, _dp, _ip]
     L.orc_step_vjp.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, d, i, _dp,
                                _dp, _dp, _dp]
     L.orc_step_jvp.argtypes = L.orc_step_vjp.argtypes
@@ -152,6 +158,10 @@ class Geometry:
         if rc != 0:
             raise ValueError("oracle: degenerate mesh")
 
+        # centroid-to-face-midpoint offsets of the second-order reconstruction
+        self.r = np.zeros((Cc, 3, 2))
+        lib().orc_mesh_face_offsets(xy.shape[0], _d(xy), Cc, _i(tri), _d(self.r))
+
     def cfl_dt(self, cfl: float) -> float:
         return float(cfl * np.min(2.0 * self.area / self.perim))
 
@@ -191,6 +201,31 @@ def flux_update(T: Tables, G: Geometry, psi, u, sigma_a, sigma_s, qsrc, dt, bc=0
                           _d(np.ascontiguousarray(sigma_s, dtype=np.float64)),
                           _d(np.ascontiguousarray(qsrc, dtype=np.float64)), dt, bc, _d(u),
                           nthreads)
+
+
+def reconstruct(G: Geometry, psi, bc=0):
+    """Second-order reconstruction of ordinate values psi [C, Q] (Sec. 4.3): returns the unlimited
+    Green-Gauss gradients [C, Q, 2], the Barth-Jespersen limiter [C, Q] and the face values
+    [C, 3, Q]."""
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    C, Q = psi.shape
+    grad = np.zeros((C, Q, 2))
+    lim = np.zeros((C, Q))
+    psif = np.zeros((C, 3, Q))
+    lib().orc_reconstruct(C, Q, _i(G.nbr), _d(G.nrm), _d(G.area), _d(G.r), _d(psi), bc,
+                          _d(grad), _d(lim), _d(psif))
+    return grad, lim, psif
+
+
+def mn_run2(T: Tables, G: Geometry, u, alpha, sigma_a, sigma_s, qsrc, dt, nsteps, bc=0, tau=1e-10,
+            max_iter=100, polish=True, nthreads=0):
+    """nsteps second-order (reconstruction + Heun) M_N steps in place on u and alpha."""
+    st = np.zeros(G.C, dtype=np.int32)
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    nf = lib().orc_mn_run2(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                           _d(G.nrm), _d(G.area), _d(G.r), f(sigma_a), f(sigma_s), f(qsrc), dt, bc,
+                           nsteps, tau, max_iter, int(polish), nthreads, _d(u), _d(alpha), _i(st))
+    return nf, st
 
 
 def _scatter_coefficients(T: Tables, g):

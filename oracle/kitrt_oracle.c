@@ -20,6 +20,8 @@
  *     an isotropic source [Sec. 3.1 moment equations: scattering diagonal in moments].
  *   - Discrete adjoint of that step (exact transpose, closure derivative dalpha/du = H^-1), and
  *     the one-step tangent written separately in forward mode (for the transpose test).
+ *   - The second-order scheme [Sec. 4.3]: Green-Gauss gradient, Barth-Jespersen limiter,
+ *     reconstructed ordinates as the inputs of the kinetic upwind flux, Heun time stepping.
  *   - The S_N step of the nodal system [Sec. 2, Eq. SNEqns2] with the P_N form O Sigma M of the
  *     scattering operator and the same upwind flux applied per ordinate.
  *   - Plain MLP (softplus) forward/backward and Adam, for the learned-closure gradient checks.
@@ -499,6 +501,188 @@ void orc_flux_update(int C, int n, int Q, const double *M, const double *w, cons
         }
     }
     (void)nthreads;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Second-order scheme [Sec. 4.3]: linear reconstruction with the Green-Gauss gradient and the   */
+/* Barth-Jespersen limiter, second-order upwind (kinetic) flux, Heun time stepping              */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Offsets r_ik from the centroid of cell i to the midpoint of its face k (same orientation and
+ * face order as orc_mesh_geometry: counter-clockwise, face k from vertex k to vertex k+1). */
+void orc_mesh_face_offsets(int nv, const double *xy, int nc, const int32_t *tri, double *r)
+{
+    (void)nv;
+    for (int c = 0; c < nc; ++c) {
+        int v[3] = {tri[3 * c], tri[3 * c + 1], tri[3 * c + 2]};
+        double cr = (xy[2 * v[1]] - xy[2 * v[0]]) * (xy[2 * v[2] + 1] - xy[2 * v[0] + 1]) -
+                    (xy[2 * v[2]] - xy[2 * v[0]]) * (xy[2 * v[1] + 1] - xy[2 * v[0] + 1]);
+        if (cr < 0) {
+            int t = v[1];
+            v[1] = v[2];
+            v[2] = t;
+        }
+        double cx = (xy[2 * v[0]] + xy[2 * v[1]] + xy[2 * v[2]]) / 3.0;
+        double cy = (xy[2 * v[0] + 1] + xy[2 * v[1] + 1] + xy[2 * v[2] + 1]) / 3.0;
+        for (int k = 0; k < 3; ++k) {
+            int a = v[k], b = v[(k + 1) % 3];
+            r[6 * c + 2 * k] = 0.5 * (xy[2 * a] + xy[2 * b]) - cx;
+            r[6 * c + 2 * k + 1] = 0.5 * (xy[2 * a + 1] + xy[2 * b + 1]) - cy;
+        }
+    }
+}
+
+/* Value of ordinate q of the cell across face k of cell i: the neighbour's cell value, or the
+ * boundary ghost (Neumann: the cell's own value; vacuum: 0). */
+static double orc_across(const int32_t *nbr, int Q, const double *psi, int bc, int i, int k, int q)
+{
+    int j = nbr[3 * i + k];
+    if (j >= 0) return psi[(size_t)j * Q + q];
+    return bc == 0 ? psi[(size_t)i * Q + q] : 0.0;
+}
+
+/* Reconstruction of the ordinate values psi [C x Q] (every ordinate separately, the inputs of the
+ * kinetic flux) [Sec. 4.3]:
+ *   gradient  g_i = 1/A_i sum_k 1/2 (psi_i + psi_j(k)) n_ik            (Green-Gauss, face average)
+ *   limiter   Psi_i = min_k { min(1, (max(psi_i, psi_j) - psi_i) / D)   if D > 0
+ *                             min(1, (min(psi_i, psi_j) - psi_i) / D)   if D < 0
+ *                             1                                          if D = 0 },  D = g_i . r_ik
+ *   face value psif_ik = psi_i + Psi_i g_i . r_ik.
+ * psi_j(k) across a boundary face is the ghost of orc_across. grad [C x Q x 2] and lim [C x Q]
+ * may be NULL; psif is [C x 3 x Q]. */
+void orc_reconstruct(int C, int Q, const int32_t *nbr, const double *nrm, const double *area,
+                     const double *r, const double *psi, int bc, double *grad, double *lim,
+                     double *psif)
+{
+    for (int i = 0; i < C; ++i)
+        for (int q = 0; q < Q; ++q) {
+            double pi = psi[(size_t)i * Q + q];
+            double gx = 0.0, gy = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                double avg = 0.5 * (pi + orc_across(nbr, Q, psi, bc, i, k, q));
+                gx += avg * nrm[6 * i + 2 * k];
+                gy += avg * nrm[6 * i + 2 * k + 1];
+            }
+            gx /= area[i];
+            gy /= area[i];
+            double L = 1.0;
+            for (int k = 0; k < 3; ++k) {
+                double pj = orc_across(nbr, Q, psi, bc, i, k, q);
+                double D = gx * r[6 * i + 2 * k] + gy * r[6 * i + 2 * k + 1];
+                double lk = 1.0;
+                if (D > 0.0) {
+                    double hi = pi > pj ? pi : pj;
+                    lk = (hi - pi) / D;
+                } else if (D < 0.0) {
+                    double lo = pi < pj ? pi : pj;
+                    lk = (lo - pi) / D;
+                }
+                if (lk > 1.0) lk = 1.0;
+                if (lk < L) L = lk;
+            }
+            if (grad) {
+                grad[((size_t)i * Q + q) * 2] = gx;
+                grad[((size_t)i * Q + q) * 2 + 1] = gy;
+            }
+            if (lim) lim[(size_t)i * Q + q] = L;
+            for (int k = 0; k < 3; ++k)
+                psif[((size_t)i * 3 + k) * Q + q] =
+                    pi + L * (gx * r[6 * i + 2 * k] + gy * r[6 * i + 2 * k + 1]);
+        }
+}
+
+/* Explicit update with the second-order kinetic flux [Sec. 4.3, Sec. 4.4]: the upwind flux of
+ * Eq. upwind1stOrder at every quadrature point with the reconstructed face values as its inputs,
+ *   F_i = sum_k sum_q w_q m_q (Omega_q . n_ik) [psif_ik,q H(Omega_q . n_ik)
+ *                                               + psif_j(k)k',q (1 - H(Omega_q . n_ik))],
+ * k' the face of the neighbour j shared with cell i; across a boundary face the outside value is
+ * psif_ik,q (Neumann) or 0 (vacuum). Then uout_i = uin_i - dt/A_i F_i + dt R_i(uin_i) with the
+ * source of orc_flux_update. */
+void orc_flux_update2(int C, int n, int Q, const double *M, const double *w, const double *ox,
+                      const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+                      const double *psif, const double *sigma_a, const double *sigma_s,
+                      const double *qsrc, double dt, int bc, const double *uin, double *uout)
+{
+    double mbar[64];
+    for (int a = 0; a < n; ++a) {
+        mbar[a] = 0.0;
+        for (int q = 0; q < Q; ++q) mbar[a] += w[q] * M[(size_t)q * n + a];
+    }
+    for (int i = 0; i < C; ++i) {
+        double F[64];
+        for (int a = 0; a < n; ++a) F[a] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            int j = nbr[3 * i + k];
+            int kk = -1;
+            if (j >= 0)
+                for (int t = 0; t < 3; ++t)
+                    if (nbr[3 * j + t] == i) kk = t;
+            double nx = nrm[6 * i + 2 * k], ny = nrm[6 * i + 2 * k + 1];
+            for (int q = 0; q < Q; ++q) {
+                double dot = ox[q] * nx + oy[q] * ny;
+                double own = psif[((size_t)i * 3 + k) * Q + q];
+                double up;
+                if (dot > 0.0)
+                    up = own;
+                else if (j >= 0)
+                    up = psif[((size_t)j * 3 + kk) * Q + q];
+                else
+                    up = (bc == 0) ? own : 0.0;
+                double s = w[q] * dot * up;
+                for (int a = 0; a < n; ++a) F[a] += s * M[(size_t)q * n + a];
+            }
+        }
+        const double *ui = uin + (size_t)i * n;
+        double u0 = ui[0];
+        for (int a = 0; a < n; ++a) {
+            double R = -sigma_a[i] * ui[a] - sigma_s[i] * (ui[a] - (a == 0 ? u0 : 0.0)) +
+                       qsrc[i] * mbar[a];
+            uout[(size_t)i * n + a] = ui[a] - dt / area[i] * F[a] + dt * R;
+        }
+    }
+}
+
+/* nsteps second-order M_N steps [Sec. 4.3, Heun]: with L(u) = -F(psif(alpha(u)))/A + R(u),
+ *   u* = u^n + dt L(u^n),  u** = u* + dt L(u*),  u^{n+1} = (u^n + u**) / 2
+ * (the paper's Delta t / A_i R in the Heun stages reads as Delta t R, as in the first-order
+ * iteration). Each stage closes its moments (warm start: the previous closure), builds the
+ * ansatz, reconstructs it and applies the second-order flux. Returns the number of failed
+ * closures. */
+int orc_mn_run2(int C, int n, int Q, const double *M, const double *w, const double *ox,
+                const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+                const double *r, const double *sigma_a, const double *sigma_s, const double *qsrc,
+                double dt, int bc, int nsteps, double tau, int max_iter, int polish, int nthreads,
+                double *u, double *alpha, int32_t *status)
+{
+    size_t Cn = (size_t)C * n;
+    double *psi = (double *)malloc(sizeof(double) * (size_t)C * Q);
+    double *psif = (double *)malloc(sizeof(double) * (size_t)C * 3 * Q);
+    double *u0 = (double *)malloc(sizeof(double) * Cn);
+    double *us = (double *)malloc(sizeof(double) * Cn);
+    double *uss = (double *)malloc(sizeof(double) * Cn);
+    int nfail = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        memcpy(u0, u, sizeof(double) * Cn);
+        nfail += orc_closure_batch(C, n, Q, M, w, u0, alpha, tau, max_iter, 30, 1e-4, polish,
+                                   nthreads, status, NULL);
+        orc_ansatz(C, n, Q, M, alpha, psi, nthreads);
+        orc_reconstruct(C, Q, nbr, nrm, area, r, psi, bc, NULL, NULL, psif);
+        orc_flux_update2(C, n, Q, M, w, ox, oy, nbr, nrm, area, psif, sigma_a, sigma_s, qsrc, dt,
+                         bc, u0, us);
+        nfail += orc_closure_batch(C, n, Q, M, w, us, alpha, tau, max_iter, 30, 1e-4, polish,
+                                   nthreads, status, NULL);
+        orc_ansatz(C, n, Q, M, alpha, psi, nthreads);
+        orc_reconstruct(C, Q, nbr, nrm, area, r, psi, bc, NULL, NULL, psif);
+        orc_flux_update2(C, n, Q, M, w, ox, oy, nbr, nrm, area, psif, sigma_a, sigma_s, qsrc, dt,
+                         bc, us, uss);
+        for (size_t k = 0; k < Cn; ++k) u[k] = 0.5 * (u0[k] + uss[k]);
+    }
+    free(psi);
+    free(psif);
+    free(u0);
+    free(us);
+    free(uss);
+    return nfail;
 }
 
 /* ------------------------------------------------------------------------------------------ */
