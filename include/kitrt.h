@@ -81,6 +81,12 @@ typedef struct {
     int32_t polish;        /* 1: one extra full Newton step after the test passes */
     double cfl;            /* dt = cfl * min_i 2 A_i / P_i when kitrt_step gets dt <= 0 */
     double fallback_tol;   /* KITRT_LEARNED: accept the MLP when ||<m psi> - u|| <= tol ||u|| */
+    int32_t order;         /* 1: first-order upwind flux and forward Euler [Sec. 4.2];
+                              2: second order in space and time [Sec. 4.3]: the ansatz at every
+                              quadrature point reconstructed linearly per cell (Green-Gauss
+                              gradient, Barth-Jespersen limiter), upwind flux of the
+                              reconstructed face values, Heun time stepping (two closures per
+                              step) */
 } kitrt_mn_params;
 
 /* Counters of the last call (filled only when a non-null pointer is passed; doing so
@@ -110,7 +116,8 @@ typedef struct {
 const char *kitrt_status_string(int32_t code);
 
 /* Fill `p` with the defaults used by the library's tests: N=2, order 10, FP64, Neumann,
- * tau 1e-10, max_iter 100, 30 halvings, c1 1e-4, polish on, CFL 0.4, fallback_tol 1e-6. */
+ * tau 1e-10, max_iter 100, 30 halvings, c1 1e-4, polish on, CFL 0.4, fallback_tol 1e-6, first
+ * order in space and time. */
 int32_t kitrt_default_params(kitrt_mn_params *p);
 
 /* Build a triangle mesh [Sec. 4.1: cell-centred unstructured grid with centroid, area A_i,
@@ -216,7 +223,8 @@ int32_t kitrt_ansatz(kitrt_mn *mn, const double *alpha, double *psi, void *strea
  * every cell from the alpha it is given, whatever its contents. */
 int32_t kitrt_mn_reset(kitrt_mn *mn);
 
-/* nsteps explicit M_N steps, in place:
+/* nsteps explicit M_N steps, in place (order 1; with order 2 each step is the Heun scheme of
+ * Sec. 4.3 described after the argument list):
  *   u^{n+1}_i = u^n_i - dt/A_i sum_{j in N(i)} F_up(psi_i, psi_j) + dt R_i(u^n_i),
  *   R_i(u) = -sigma_a,i u - sigma_s,i (u - u_0 e_0) + q_i <m>,
  * with F_up the kinetic upwind flux of the closed ansatz [Sec. 4.4] and psi the closure of u^n
@@ -239,6 +247,11 @@ int32_t kitrt_mn_reset(kitrt_mn *mn);
  *           and returns KITRT_EINVAL, before u is touched, when a cell violates it or has a
  *           negative or non-finite coefficient.
  *   status  device [C] or NULL: per-cell status of the last failed closure.
+ * Order 2 [Sec. 4.3]: u* = u + dt L(u), u <- (u + u* + dt L(u*)) / 2, where L(v) closes v, builds
+ * the ansatz, reconstructs it linearly in every cell at every quadrature point (Green-Gauss
+ * gradient from face averages, Barth-Jespersen limiter with the two cells of each face as bounds,
+ * so every face value lies between them) and applies the upwind flux of the face values plus
+ * R(v); two closures per step (the second continues from the first).
  * Synchronises with `stream` once per step (closure completion test). On a closure failure the
  * step stops before updating u with that closure and returns its status. */
 int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a,

@@ -190,7 +190,8 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
                                  double *dJ_dsa, double *dJ_dss, void *stream)
 {
     if (!mn || !u0 || !alpha0 || !sigma_a || !sigma_s || !q || !block_of_cell || !target || !J ||
-        !dJ_dsa || !dJ_dss || nblocks < 1 || nsteps < 0 || ckpt_every < 1 || mn->p.mode != KITRT_FP64)
+        !dJ_dsa || !dJ_dss || nblocks < 1 || nsteps < 0 || ckpt_every < 1 || mn->p.mode != KITRT_FP64 ||
+        mn->p.order != 1)
         return KITRT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int C = mn->mesh->C, n = mn->n, Qp = mn->Qp;

@@ -222,7 +222,8 @@ LaunchScope::~LaunchScope()
 
 static const char *kProfNames[PK_COUNT] = {"closure_begin", "closure_eval_fp64", "closure_finish",
                                            "flux_update", "closure_eval_mixed", "mlp",
-                                           "adjoint", "other", "closure_newton", "sn_step"};
+                                           "adjoint", "other", "closure_newton", "sn_step",
+                                           "reconstruct"};
 
 Tables kitrt_mn::tables() const
 {
@@ -289,6 +290,7 @@ int32_t kitrt_default_params(kitrt_mn_params *p)
     p->polish = 1;
     p->cfl = 0.4;
     p->fallback_tol = 1e-6;
+    p->order = 1;
     return KITRT_OK;
 }
 
@@ -305,6 +307,7 @@ int32_t kitrt_mesh_create(const double *xy, int32_t nverts, const int32_t *tri, 
     m->cen.resize(2 * (size_t)ntri);
     m->nrm.resize(6 * (size_t)ntri);
     m->nbr.assign(3 * (size_t)ntri, -1);
+    m->r.resize(6 * (size_t)ntri);
     std::unordered_map<uint64_t, int64_t> open_edge;  // edge key -> cell*3+face
     open_edge.reserve((size_t)ntri * 2);
     double minr = 1e300;
@@ -331,6 +334,9 @@ int32_t kitrt_mesh_create(const double *xy, int32_t nverts, const int32_t *tri, 
         for (int k = 0; k < 3; ++k) {
             int32_t a = v[k], b = v[(k + 1) % 3];
             double dx = xy[2 * b] - xy[2 * a], dy = xy[2 * b + 1] - xy[2 * a + 1];
+            // centroid to face midpoint (second-order reconstruction)
+            m->r[6 * (size_t)c + 2 * k] = 0.5 * (xy[2 * a] + xy[2 * b]) - m->cen[2 * c];
+            m->r[6 * (size_t)c + 2 * k + 1] = 0.5 * (xy[2 * a + 1] + xy[2 * b + 1]) - m->cen[2 * c + 1];
             // outward normal of edge a->b of a counter-clockwise triangle, |n| = edge length
             m->nrm[6 * (size_t)c + 2 * k] = xy[2 * b + 1] - xy[2 * a + 1];
             m->nrm[6 * (size_t)c + 2 * k + 1] = xy[2 * a] - xy[2 * b];
@@ -360,22 +366,42 @@ int32_t kitrt_mesh_create(const double *xy, int32_t nverts, const int32_t *tri, 
         return rc;
     }
     m->min_inradius = minr;
+    // .w packs, for each face k, the neighbour's index of the shared face (2 bits at 2k)
     std::vector<int4> nb4(ntri);
-    for (int32_t c = 0; c < ntri; ++c)
-        nb4[c] = make_int4(m->nbr[3 * c], m->nbr[3 * c + 1], m->nbr[3 * c + 2], 0);
+    for (int32_t c = 0; c < ntri; ++c) {
+        int packed = 0;
+        for (int k = 0; k < 3; ++k) {
+            const int j = m->nbr[3 * c + k];
+            if (j < 0) continue;
+            for (int t = 0; t < 3; ++t)
+                if (m->nbr[3 * (size_t)j + t] == c) packed |= t << (2 * k);
+        }
+        nb4[c] = make_int4(m->nbr[3 * c], m->nbr[3 * c + 1], m->nbr[3 * c + 2], packed);
+    }
     std::vector<double> hpa(ntri);
-    std::vector<float> nrm32(6 * (size_t)ntri), inva32(ntri);
+    std::vector<float> nrm32(6 * (size_t)ntri), inva32(ntri), r32(6 * (size_t)ntri);
+    std::vector<double> inva(ntri);
     for (int32_t c = 0; c < ntri; ++c) {
         hpa[c] = m->perim[c] / (2.0 * m->area[c]);
+        inva[c] = 1.0 / m->area[c];
         inva32[c] = (float)(1.0 / m->area[c]);
-        for (int k = 0; k < 6; ++k) nrm32[6 * (size_t)c + k] = (float)m->nrm[6 * (size_t)c + k];
+        for (int k = 0; k < 6; ++k) {
+            nrm32[6 * (size_t)c + k] = (float)m->nrm[6 * (size_t)c + k];
+            r32[6 * (size_t)c + k] = (float)m->r[6 * (size_t)c + k];
+        }
     }
     bool ok = cudaMalloc(&m->d_nbr, sizeof(int4) * ntri) == cudaSuccess &&
               cudaMalloc(&m->d_nrm, sizeof(double) * 6 * ntri) == cudaSuccess &&
               cudaMalloc(&m->d_area, sizeof(double) * ntri) == cudaSuccess &&
               cudaMalloc(&m->d_hpa, sizeof(double) * ntri) == cudaSuccess &&
               cudaMalloc(&m->d_nrm32, sizeof(float) * 6 * ntri) == cudaSuccess &&
-              cudaMalloc(&m->d_inva32, sizeof(float) * ntri) == cudaSuccess;
+              cudaMalloc(&m->d_inva32, sizeof(float) * ntri) == cudaSuccess &&
+              cudaMalloc(&m->d_inva, sizeof(double) * ntri) == cudaSuccess &&
+              cudaMalloc(&m->d_r, sizeof(double) * 6 * ntri) == cudaSuccess &&
+              cudaMalloc(&m->d_r32, sizeof(float) * 6 * ntri) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_inva, inva.data(), sizeof(double) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_r, m->r.data(), sizeof(double) * 6 * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->d_r32, r32.data(), sizeof(float) * 6 * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_nrm32, nrm32.data(), sizeof(float) * 6 * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_inva32, inva32.data(), sizeof(float) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(m->d_hpa, hpa.data(), sizeof(double) * ntri, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -399,6 +425,9 @@ int32_t kitrt_mesh_destroy(kitrt_mesh *m)
     cudaFree(m->d_hpa);
     cudaFree(m->d_nrm32);
     cudaFree(m->d_inva32);
+    cudaFree(m->d_inva);
+    cudaFree(m->d_r);
+    cudaFree(m->d_r32);
     delete m;
     return KITRT_OK;
 }
@@ -442,7 +471,8 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     const kitrt_mn_params &p = *params;
     if (p.degree < 1 || p.degree > KITRT_MAX_DEGREE || p.quad_order < p.degree + 1 ||
         p.quad_order > 64 || !(p.tau > 0) || p.max_iter < 1 || p.max_halvings < 0 ||
-        p.mode < KITRT_FP64 || p.mode > KITRT_LEARNED || (p.bc != 0 && p.bc != 1))
+        p.mode < KITRT_FP64 || p.mode > KITRT_LEARNED || (p.bc != 0 && p.bc != 1) ||
+        (p.order != 1 && p.order != 2))
         return KITRT_EINVAL;
     kitrt_mn *mn = new kitrt_mn();
     mn->mesh = mesh;
@@ -690,6 +720,18 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
         TRY(dev_alloc(mn, &cellc, C * 12));
         mn->d_sn_cell = cellc;
     }
+    if (p.order == 2) {
+        TRY(dev_alloc(mn, &mn->d_ustage, C * n));
+        if (p.mode == KITRT_FP64) {
+            double *pf = nullptr;
+            TRY(dev_alloc(mn, &pf, C * 3 * Qp));
+            mn->d_psif = pf;
+        } else {
+            float *pf = nullptr;
+            TRY(dev_alloc(mn, &pf, C * 3 * Qp));
+            mn->d_psif = pf;
+        }
+    }
     TRY(dev_alloc(mn, &mn->d_check, 2));
     if (cudaMallocHost(&mn->h_check, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         kitrt_mn_destroy(mn);
@@ -914,7 +956,29 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
     // back with the first closure's completion counters, before u is touched
     int rc = check_stability(mn, sigma_a, sigma_s, dt, s, false);
     if (rc) return rc;
-    for (int32_t it = 0; it < nsteps; ++it) {
+    for (int32_t it = 0; it < nsteps && mn->p.order == 2; ++it) {
+        // Heun [Sec. 4.3]: u* = u + dt L(u), u <- (u + u* + dt L(u*)) / 2, each stage with its
+        // own closure (the second continues from the first), reconstruction and flux
+        const bool fp64 = mn->p.mode == KITRT_FP64;
+        const void *psi = fp64 ? (const void *)mn->d_psi : (const void *)mn->d_psi32;
+        for (int stage = 0; stage < 2 && !rc; ++stage) {
+            double *uin = stage == 0 ? u : mn->d_ustage;
+            rc = run_closure(mn, C, uin, alpha, it == 0 && stage == 0 ? first : 0, s, stats,
+                             fp64 ? nullptr : mn->d_psi32);
+            if (!rc && it == 0 && stage == 0) rc = stability_verdict(mn);
+            if (!rc)
+                rc = launch_finish(mn, T, mn->st, C, alpha, fp64 ? mn->d_psi : nullptr, nullptr,
+                                   polish_of(mn), it > 0 || stage > 0, s);
+            if (!rc) rc = launch_recon(mn, T, psi, mn->d_psif, !fp64, mn->p.bc, s);
+            if (!rc)
+                rc = stage == 0 ? launch_flux2(mn, T, psi, mn->d_psif, !fp64, u, nullptr, mn->d_ustage,
+                                               sigma_a, sigma_s, q, dt, 0.0, 1.0, mn->p.bc, s)
+                                : launch_flux2(mn, T, psi, mn->d_psif, !fp64, mn->d_ustage, u, u,
+                                               sigma_a, sigma_s, q, dt, 0.5, 0.5, mn->p.bc, s);
+        }
+        if (rc) break;
+    }
+    for (int32_t it = 0; it < nsteps && mn->p.order == 1; ++it) {
         const bool fp64 = mn->p.mode == KITRT_FP64;
         // mixed modes: the evaluation sweeps write the FP32 ansatz of every accepted point, and
         // with no polish step the solution's ansatz is already in place

@@ -27,14 +27,18 @@ struct kitrt_mesh {
     int32_t C = 0;
     int device = 0;
     double min_inradius = 0.0;
-    std::vector<double> area, perim, cen, nrm;
+    std::vector<double> area, perim, cen, nrm, r;
     std::vector<int32_t> nbr;
-    int4 *d_nbr = nullptr;     // [C] neighbours across faces 0..2 (-1 = boundary), .w unused
+    int4 *d_nbr = nullptr;     // [C] neighbours across faces 0..2 (-1 = boundary); .w: the
+                               // neighbour's index of each shared face, 2 bits per face
     double *d_nrm = nullptr;   // [C x 6] scaled outward normals (nx0, ny0, nx1, ny1, nx2, ny2)
     double *d_area = nullptr;  // [C]
     double *d_hpa = nullptr;   // [C] P_i / (2 A_i): largest outflow rate of the cell per unit speed
     float *d_nrm32 = nullptr;  // [C x 6] FP32 copy of the scaled normals (FP32 flux)
     float *d_inva32 = nullptr; // [C] FP32 1 / A_i
+    double *d_inva = nullptr;  // [C] 1 / A_i
+    double *d_r = nullptr;     // [C x 6] centroid-to-face-midpoint offsets (second order)
+    float *d_r32 = nullptr;    // FP32 copy
 };
 
 // Device views handed to kernels by value.
@@ -93,7 +97,7 @@ struct NewtonParams {
 // Kernel kinds recorded by the tracer.
 enum ProfKind : int { PK_BEGIN = 0, PK_EVAL = 1, PK_FINISH = 2, PK_FLUX = 3, PK_EVAL_MIXED = 4,
                       PK_MLP = 5, PK_ADJOINT = 6, PK_OTHER = 7, PK_POST = 8, PK_SN = 9,
-                      PK_COUNT = 10 };
+                      PK_RECON = 10, PK_COUNT = 11 };
 
 struct ProfRec {
     int kind;
@@ -132,6 +136,8 @@ struct kitrt_mn {
     // workspace
     NewtonState st{};
     double *d_psi = nullptr;   // [C x Qp] FP64 ansatz
+    void *d_psif = nullptr;    // second order: [C x 3 x Qp] reconstructed face values (FP64/FP32)
+    double *d_ustage = nullptr;  // second order: [C x n] the Heun stage u*
     float *d_psi32 = nullptr;  // [C x Qp] FP32 ansatz (mixed modes)
     int32_t *h_cnt = nullptr;  // pinned copy of st.cnt
     // kitrt_mn_reset: the next kitrt_step starts every cell from its given alpha (otherwise each
@@ -239,6 +245,12 @@ int launch_moments_mixed(kitrt_mn *mn, const Tables &T, int C, const double *alp
 int check_stability(kitrt_mn *mn, const double *sa, const double *ss, double dt, cudaStream_t s,
                     bool wait);
 int stability_verdict(const kitrt_mn *mn);
+int launch_recon(kitrt_mn *mn, const Tables &T, const void *psi, void *psif, bool fp32, int bc,
+                 cudaStream_t s);
+int launch_flux2(kitrt_mn *mn, const Tables &T, const void *psi, const void *psif, bool fp32,
+                 const double *uin, const double *base, double *uout, const double *sa,
+                 const double *ss, const double *q, double dt, double c0, double c1, int bc,
+                 cudaStream_t s);
 int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
                        const float *psi32, double *u, const double *sa, const double *ss,
                        const double *q, double dt, int bc, cudaStream_t s);
