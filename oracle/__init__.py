@@ -59,6 +59,10 @@ def _declare(L):
     L.orc_tables.argtypes = [i, i, _dp, _dp, _dp, _dp]
     L.orc_mesh_geometry.argtypes = [i, _dp, i, _ip, _dp, _dp, _dp, _ip, _dp]
     L.orc_closure_batch.argtypes = [i, i, i, _dp, _dp, _dp, _dp, d, i, i, d, i, i, _ip, _ip]
+    L.orc_closure_batch_reg.argtypes = [i, i, i, _dp, _dp, _dp, _dp, d, i, i, d, i, d, i, i, _ip,
+                                        _ip]
+    L.orc_mn_run_reg.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, d, i,
+                                 i, d, i, i, d, i, i, _dp, _dp, _ip]
     L.orc_isotropic_alpha.argtypes = [i, i, d, _dp, _dp]
     L.orc_ansatz.argtypes = [i, i, i, _dp, _dp, _dp, i]
     L.orc_flux_update.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
@@ -177,6 +181,32 @@ def closure(T: Tables, u: np.ndarray, alpha: np.ndarray, tau=1e-10, max_iter=100
     lib().orc_closure_batch(Cc, T.n, T.Q, _d(T.M), _d(T.w), _d(u), _d(alpha), tau, max_iter,
                             max_halvings, c1, int(polish), nthreads, _i(st), _i(it))
     return st, it
+
+
+def closure_reg(T: Tables, u: np.ndarray, alpha: np.ndarray, gamma: float, reg0: int = 1,
+                tau=1e-10, max_iter=100, polish=True, nthreads=0, max_halvings=30, c1=1e-4):
+    """The (partially) regularized closure of every row of u (Sec. 3.1, Eq. entropyOCP_reg with
+    reg0 = 0, Eq. entropyOCP_part_reg with reg0 = 1: u_0 kept exact). Returns (status, iters)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    Cc = u.shape[0]
+    st = np.zeros(Cc, dtype=np.int32)
+    it = np.zeros(Cc, dtype=np.int32)
+    lib().orc_closure_batch_reg(Cc, T.n, T.Q, _d(T.M), _d(T.w), _d(u), _d(alpha), tau, max_iter,
+                                max_halvings, c1, int(polish), float(gamma), int(reg0), nthreads,
+                                _i(st), _i(it))
+    return st, it
+
+
+def mn_run_reg(T: Tables, G: Geometry, u, alpha, sigma_a, sigma_s, qsrc, dt, nsteps, gamma,
+               reg0=1, bc=0, tau=1e-10, max_iter=100, polish=True, nthreads=0):
+    """nsteps first-order M_N steps with the (partially) regularized closure, in place."""
+    st = np.zeros(G.C, dtype=np.int32)
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    nf = lib().orc_mn_run_reg(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                              _d(G.nrm), _d(G.area), f(sigma_a), f(sigma_s), f(qsrc), dt, bc,
+                              nsteps, tau, max_iter, int(polish), float(gamma), int(reg0),
+                              nthreads, _d(u), _d(alpha), _i(st))
+    return nf, st
 
 
 def isotropic_alpha(T: Tables, u: np.ndarray) -> np.ndarray:

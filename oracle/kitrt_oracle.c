@@ -14,7 +14,8 @@
  *   - Cell-centred triangle geometry: areas A_i, neighbours N(i), scaled normals n_ij [Sec. 4.1].
  *   - Entropy closure [Sec. 3.1, Eq. entropyOCP] with the Maxwell-Boltzmann entropy, solved
  *     through its dual f(alpha) = <exp(alpha.m)> - alpha.u by damped Newton with an Armijo line
- *     search [Sec. 7.2 M_N run: "Newton optimizer with line search"].
+ *     search [Sec. 7.2 M_N run: "Newton optimizer with line search"]; optionally (partially)
+ *     regularized [Sec. 3.1, Eq. entropyOCP_reg, Eq. entropyOCP_part_reg].
  *   - Kinetic upwind flux of the closed ansatz [Sec. 4.4, last flux equation] and the explicit
  *     first-order update [Sec. 4.2, explicit iteration] with isotropic scattering, absorption and
  *     an isotropic source [Sec. 3.1 moment equations: scattering diagonal in moments].
@@ -270,6 +271,9 @@ typedef struct {
     int max_halvings; /* Armijo backtracking halvings per iteration */
     double c1;        /* Armijo constant */
     int polish;       /* one extra full Newton step after the test passes */
+    double gamma;     /* regularization parameter (0: the entropy closure itself) */
+    int reg0;         /* first regularized moment: 0 (all, Eq. entropyOCP_reg) or 1 (u_0 kept
+                         exact, Eq. entropyOCP_part_reg) */
 } orc_newton_opts;
 
 /* Dual objective and its derivatives at alpha over the full quadrature:
@@ -302,6 +306,29 @@ static void orc_dual_eval(int n, int Q, const double *M, const double *w, const 
         for (int a = 0; a < n; ++a) g[a] -= u[a];
     if (f) *f = s - au;
     if (fmag) *fmag = s + fabs(au);
+}
+
+/* The (partially) regularized closure [Sec. 3.1, Eq. entropyOCP_reg and Eq. entropyOCP_part_reg]:
+ * the primal adds 1/(2 gamma) ||<m^r g> - u^r||^2 to the entropy (r = the regularized moments)
+ * and drops their moment constraints. Eliminating the slack v = <m^r g> - u^r from the
+ * Lagrangian, min_v ||v||^2 / (2 gamma) + alpha^r . v = -gamma ||alpha^r||^2 / 2, so the dual to
+ * minimise becomes
+ *   f(alpha) = <exp(alpha.m)> - alpha.u + gamma/2 ||alpha^r||^2,
+ *   g = <m e> - u + gamma alpha^r,   H = <m m^T e> + gamma I_r,
+ * and the regularized ansatz exp(alpha.m) has moments <m^r psi> = u^r - gamma alpha^r. Adds the
+ * regularization terms to f, g, H, fmag (any may be NULL) at alpha; r = {reg0, ..., n-1}. */
+static void orc_dual_regularize(int n, double gamma, int reg0, const double *alpha, double *f,
+                                double *g, double *H, double *fmag)
+{
+    if (gamma == 0.0) return;
+    double a2 = 0.0;
+    for (int a = reg0; a < n; ++a) a2 += alpha[a] * alpha[a];
+    if (f) *f += 0.5 * gamma * a2;
+    if (fmag) *fmag += 0.5 * gamma * a2;
+    if (g)
+        for (int a = reg0; a < n; ++a) g[a] += gamma * alpha[a];
+    if (H)
+        for (int a = reg0; a < n; ++a) H[a * n + a] += gamma;
 }
 
 /* Cholesky H = L L^T (L lower, row-major in L[a*n+b], b <= a). Returns 0 or -1 on a
@@ -363,6 +390,7 @@ int orc_closure_solve(int n, int Q, const double *M, const double *w, const doub
     int it = 0;
     if (iters) *iters = 0;
     orc_dual_eval(n, Q, M, w, u, alpha, &f, g, H, &fmag);
+    orc_dual_regularize(n, o->gamma, o->reg0, alpha, &f, g, H, &fmag);
     for (;;) {
         if (!isfinite(f) || !orc_finite(n, g)) return ORC_NONFINITE;
         double gn = 0.0;
@@ -385,6 +413,7 @@ int orc_closure_solve(int n, int Q, const double *M, const double *w, const doub
         for (int h = 0; h <= o->max_halvings; ++h) {
             for (int a = 0; a < n; ++a) at[a] = alpha[a] + lam * d[a];
             orc_dual_eval(n, Q, M, w, u, at, &ft, NULL, NULL, NULL);
+            orc_dual_regularize(n, o->gamma, o->reg0, at, &ft, NULL, NULL, NULL);
             if (isfinite(ft) && ft <= f + o->c1 * lam * gd + 64.0 * 2.220446049250313e-16 * fmag) {
                 accepted = 1;
                 break;
@@ -395,16 +424,19 @@ int orc_closure_solve(int n, int Q, const double *M, const double *w, const doub
         for (int a = 0; a < n; ++a) alpha[a] = at[a];
         ++it;
         orc_dual_eval(n, Q, M, w, u, alpha, &f, g, H, &fmag);
+        orc_dual_regularize(n, o->gamma, o->reg0, alpha, &f, g, H, &fmag);
     }
 }
 
-/* Batch closure over C cells (u, alpha row-major [C x n]). status[c] gets the code; returns the
+/* Batch closure over C cells (u, alpha row-major [C x n]), regularized with (gamma, reg0) as in
+ * orc_dual_regularize (gamma = 0: the entropy closure). status[c] gets the code; returns the
  * number of failed cells. iters may be NULL. */
-int orc_closure_batch(int C, int n, int Q, const double *M, const double *w, const double *u,
-                      double *alpha, double tau, int max_iter, int max_halvings, double c1,
-                      int polish, int nthreads, int32_t *status, int32_t *iters)
+int orc_closure_batch_reg(int C, int n, int Q, const double *M, const double *w, const double *u,
+                          double *alpha, double tau, int max_iter, int max_halvings, double c1,
+                          int polish, double gamma, int reg0, int nthreads, int32_t *status,
+                          int32_t *iters)
 {
-    orc_newton_opts o = {tau, max_iter, max_halvings, c1, polish};
+    orc_newton_opts o = {tau, max_iter, max_halvings, c1, polish, gamma, reg0};
     int nfail = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -419,6 +451,15 @@ int orc_closure_batch(int C, int n, int Q, const double *M, const double *w, con
     }
     (void)nthreads;
     return nfail;
+}
+
+/* The entropy closure of every cell (no regularization). */
+int orc_closure_batch(int C, int n, int Q, const double *M, const double *w, const double *u,
+                      double *alpha, double tau, int max_iter, int max_halvings, double c1,
+                      int polish, int nthreads, int32_t *status, int32_t *iters)
+{
+    return orc_closure_batch_reg(C, n, Q, M, w, u, alpha, tau, max_iter, max_halvings, c1, polish,
+                                 0.0, 1, nthreads, status, iters);
 }
 
 /* Isotropic closed form of the closure: psi = u_0 / (4 pi m_0) constant, so
@@ -774,23 +815,34 @@ void orc_sn_run(int C, int n, int N, int Q, const double *M, const double *w, co
  * kinetic flux + update. alpha holds the closure of the last u that was closed. Returns the
  * number of failed closures summed over steps (0 on success); status gets the last failure
  * code per cell. */
-int orc_mn_run(int C, int n, int Q, const double *M, const double *w, const double *ox,
-               const double *oy, const int32_t *nbr, const double *nrm, const double *area,
-               const double *sigma_a, const double *sigma_s, const double *qsrc, double dt, int bc,
-               int nsteps, double tau, int max_iter, int polish, int nthreads, double *u,
-               double *alpha, int32_t *status)
+int orc_mn_run_reg(int C, int n, int Q, const double *M, const double *w, const double *ox,
+                   const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+                   const double *sigma_a, const double *sigma_s, const double *qsrc, double dt,
+                   int bc, int nsteps, double tau, int max_iter, int polish, double gamma,
+                   int reg0, int nthreads, double *u, double *alpha, int32_t *status)
 {
     double *psi = (double *)malloc(sizeof(double) * (size_t)C * Q);
     int nfail = 0;
     for (int s = 0; s < nsteps; ++s) {
-        nfail += orc_closure_batch(C, n, Q, M, w, u, alpha, tau, max_iter, 30, 1e-4, polish,
-                                   nthreads, status, NULL);
+        nfail += orc_closure_batch_reg(C, n, Q, M, w, u, alpha, tau, max_iter, 30, 1e-4, polish,
+                                       gamma, reg0, nthreads, status, NULL);
         orc_ansatz(C, n, Q, M, alpha, psi, nthreads);
         orc_flux_update(C, n, Q, M, w, ox, oy, nbr, nrm, area, psi, sigma_a, sigma_s, qsrc, dt,
                         bc, u, nthreads);
     }
     free(psi);
     return nfail;
+}
+
+/* nsteps first-order M_N steps with the entropy closure (no regularization). */
+int orc_mn_run(int C, int n, int Q, const double *M, const double *w, const double *ox,
+               const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+               const double *sigma_a, const double *sigma_s, const double *qsrc, double dt, int bc,
+               int nsteps, double tau, int max_iter, int polish, int nthreads, double *u,
+               double *alpha, int32_t *status)
+{
+    return orc_mn_run_reg(C, n, Q, M, w, ox, oy, nbr, nrm, area, sigma_a, sigma_s, qsrc, dt, bc,
+                          nsteps, tau, max_iter, polish, 0.0, 1, nthreads, u, alpha, status);
 }
 
 /* ------------------------------------------------------------------------------------------ */
