@@ -87,6 +87,14 @@ typedef struct {
                               gradient, Barth-Jespersen limiter), upwind flux of the
                               reconstructed face values, Heun time stepping (two closures per
                               step) */
+    double reg_gamma;      /* (partially) regularized closure [Sec. 3.1, Eq. entropyOCP_reg and
+                              Eq. entropyOCP_part_reg] with parameter gamma (0: the entropy
+                              closure). Its dual is f(alpha) + gamma/2 |alpha^r|^2: the ansatz no
+                              longer reproduces the regularized moments (it has u^r - gamma alpha^r)
+                              but a minimiser exists for any u (with u_0 > 0 when it is kept).
+                              Not with KITRT_LEARNED or kitrt_adjoint. */
+    int32_t reg_keep_mass; /* 1: u_0 is not regularized (r = moments 1..n-1, the paper's partial
+                              form); 0: every moment is */
 } kitrt_mn_params;
 
 /* Counters of the last call (filled only when a non-null pointer is passed; doing so
@@ -117,7 +125,7 @@ const char *kitrt_status_string(int32_t code);
 
 /* Fill `p` with the defaults used by the library's tests: N=2, order 10, FP64, Neumann,
  * tau 1e-10, max_iter 100, 30 halvings, c1 1e-4, polish on, CFL 0.4, fallback_tol 1e-6, first
- * order in space and time. */
+ * order in space and time, no regularization (reg_gamma 0, reg_keep_mass 1). */
 int32_t kitrt_default_params(kitrt_mn_params *p);
 
 /* Build a triangle mesh [Sec. 4.1: cell-centred unstructured grid with centroid, area A_i,
@@ -203,7 +211,8 @@ int32_t kitrt_isotropic_alpha(kitrt_mn *mn, const double *u, double *alpha, void
 int32_t kitrt_closure(kitrt_mn *mn, const double *u, double *alpha, int32_t *status,
                       void *stream, kitrt_stats *stats);
 
-/* Hessian of the dual, H = <m m^T exp(alpha.m)>, of every cell at the given alpha, computed the
+/* Hessian of the dual's entropy part, H = <m m^T exp(alpha.m)> (a regularized solver's Newton
+ * step adds reg_gamma on the regularized diagonal), of every cell at the given alpha, computed the
  * way the solver's closure computes it (FP64, or with the degree N+1..2N moments on tensor
  * cores in the mixed modes). alpha device [C x n]; H device [C x n x n] row-major, symmetric.
  * The first call allocates a [C x (2N+1)(2N+2)/2] moments buffer owned by the solver. */

@@ -92,7 +92,8 @@ begin_test_kernel(NewtonState S, const double *__restrict__ u, const double *__r
 #pragma unroll
             for (int a = 0; a < n; ++a) {
                 const double ua = u[off + a];
-                const double g = S.U[off + a] - ua;
+                double g = S.U[off + a] - ua;
+                if (a >= np.reg0) g = fma(np.gamma, S.alpha[off + a], g);
                 gn2 = fma(g, g, gn2);
                 un2 = fma(ua, ua, un2);
             }
@@ -125,7 +126,8 @@ predict_kernel(NewtonState S, const double *__restrict__ u, NewtonParams np)
         const size_t off = (size_t)cell * n;
         const double ua = lane < n ? u[off + lane] : 0.0;
         const double al = lane < n ? S.alpha[off + lane] : 0.0;
-        const double g = lane < n ? S.U[off + lane] - ua : 0.0;
+        const double g = lane < n ? fma(lane >= np.reg0 ? np.gamma : 0.0, al, S.U[off + lane] - ua) : 0.0;
+        const double ar2 = warp_sum(lane < n && lane >= np.reg0 ? al * al : 0.0);
         for (int a = lane; a < n; a += 32)
             for (int b = 0; b <= a; ++b) H[a * n + b] = S.L[(size_t)cell * npairs + tri_idx(a, b)];
         __syncwarp();
@@ -141,7 +143,7 @@ predict_kernel(NewtonState S, const double *__restrict__ u, NewtonParams np)
         if (lane == 0) {
             if (S.gnorm) S.gnorm[cell] = sqrt(gn2);
             const double fs = S.fsum[cell];
-            S.f0[cell] = fs - au;
+            S.f0[cell] = fma(0.5 * np.gamma, ar2, fs - au);
             S.gd[cell] = gd;
             S.lam[cell] = 1.0;
             S.phase[cell] = PH_NEWTON;
@@ -168,16 +170,20 @@ predict_thread_kernel(NewtonState S, const double *__restrict__ u, NewtonParams 
             cell = S.list[1][it];
             const size_t off = (size_t)cell * n;
             double Lp[npairs], y[n], g[n];
-            double gn2 = 0.0, un2 = 0.0, au = 0.0;
+            double gn2 = 0.0, un2 = 0.0, au = 0.0, ar2 = 0.0;
 #pragma unroll
             for (int p = 0; p < npairs; ++p) Lp[p] = S.L[(size_t)cell * npairs + p];
 #pragma unroll
             for (int a = 0; a < n; ++a) {
-                const double ua = u[off + a];
+                const double ua = u[off + a], al = S.alpha[off + a];
                 g[a] = S.U[off + a] - ua;
+                if (a >= np.reg0) {
+                    g[a] = fma(np.gamma, al, g[a]);
+                    ar2 = fma(al, al, ar2);
+                }
                 gn2 = fma(g[a], g[a], gn2);
                 un2 = fma(ua, ua, un2);
-                au = fma(S.alpha[off + a], ua, au);
+                au = fma(al, ua, au);
                 y[a] = -g[a];
             }
             // d = -H^-1 g with the stored factor (1/L_jj on its diagonal)
@@ -205,7 +211,7 @@ predict_thread_kernel(NewtonState S, const double *__restrict__ u, NewtonParams 
                 S.phase[cell] = PH_DONE;  // converged; d is the polish step
             } else {
                 if (S.gnorm) S.gnorm[cell] = sqrt(gn2);
-                S.f0[cell] = S.fsum[cell] - au;
+                S.f0[cell] = fma(0.5 * np.gamma, ar2, S.fsum[cell] - au);
                 S.gd[cell] = gd;
                 S.lam[cell] = 1.0;
                 S.phase[cell] = PH_NEWTON;

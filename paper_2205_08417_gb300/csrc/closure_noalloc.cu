@@ -130,7 +130,8 @@ extern "C" int32_t kitrt_closure_noalloc(const kitrt_mn *mn, const double *u, do
     view.n = mn->n;
     view.nsm = mn->nsm;
     const Tables T = mn->tables();
-    NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, mn->p.polish};
+    NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, mn->p.polish,
+                    mn->p.reg_gamma, mn->p.reg_keep_mass ? 1 : 0};
 
     if (cudaMemsetAsync(S.cnt, 0, 8 * sizeof(int32_t), s) != cudaSuccess) return KITRT_ECUDA;
     int rc = launch_begin(&view, T, S, C, u, alpha, 1, np, s);

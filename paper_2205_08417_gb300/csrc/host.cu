@@ -291,6 +291,8 @@ int32_t kitrt_default_params(kitrt_mn_params *p)
     p->cfl = 0.4;
     p->fallback_tol = 1e-6;
     p->order = 1;
+    p->reg_gamma = 0.0;
+    p->reg_keep_mass = 1;
     return KITRT_OK;
 }
 
@@ -472,7 +474,8 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     if (p.degree < 1 || p.degree > KITRT_MAX_DEGREE || p.quad_order < p.degree + 1 ||
         p.quad_order > 64 || !(p.tau > 0) || p.max_iter < 1 || p.max_halvings < 0 ||
         p.mode < KITRT_FP64 || p.mode > KITRT_LEARNED || (p.bc != 0 && p.bc != 1) ||
-        (p.order != 1 && p.order != 2))
+        (p.order != 1 && p.order != 2) || !(p.reg_gamma >= 0.0) ||
+        (p.reg_gamma > 0.0 && p.mode == KITRT_LEARNED))
         return KITRT_EINVAL;
     kitrt_mn *mn = new kitrt_mn();
     mn->mesh = mesh;
@@ -820,7 +823,8 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
                        cudaStream_t s, kitrt_stats *stats, float *psi32 = nullptr)
 {
     const Tables T = mn->tables();
-    NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, polish_of(mn)};
+    NewtonParams np{mn->p.tau, mn->p.armijo_c1, mn->p.max_iter, mn->p.max_halvings, polish_of(mn),
+                    mn->p.reg_gamma, mn->p.reg_keep_mass ? 1 : 0};
     const bool learned = mn->p.mode == KITRT_LEARNED;
     if (learned && !mn->has_mlp) return KITRT_EINVAL;
     CUDA_OK(cudaMemsetAsync(mn->st.cnt, 0, 16 * sizeof(int32_t), s));

@@ -92,6 +92,10 @@ struct NewtonState {
 struct NewtonParams {
     double tau, c1;
     int max_iter, max_halvings, polish;
+    // (partially) regularized closure: the dual gains gamma/2 |alpha^r|^2 over the moments
+    // r = reg0..n-1 (gamma = 0: the entropy closure)
+    double gamma;
+    int reg0;
 };
 
 // Kernel kinds recorded by the tracer.

@@ -109,7 +109,8 @@ __device__ void newton_post(const Tables &T, const NewtonState &S, const NewtonP
     for (int c = 0; c < n2; ++c) finite = finite && isfinite(Vs[c]);
     const double fs = Vs[0] / T.m0;
     const double au = warp_sum(at * ua);
-    const double ft = fs - au;
+    const double ar2 = warp_sum(lane < n && lane >= np.reg0 ? at * at : 0.0);
+    const double ft = fma(0.5 * np.gamma, ar2, fs - au);
     if (lane == 0) {
         const int ev = S.evals[cell] + 1;
         S.evals[cell] = ev;
@@ -156,6 +157,7 @@ __device__ void newton_post(const Tables &T, const NewtonState &S, const NewtonP
         const int b = p - a * (a + 1) / 2;
         double h = 0.0;
         for (int t = T.gstart[p]; t < T.gstart[p + 1]; ++t) h = fma(T.gcoef[t], Vs[T.gidx[t]], h);
+        if (a == b && a >= np.reg0) h += np.gamma;  // regularized moments
         H[a * n + b] = h;
         H[b * n + a] = h;
     }
@@ -184,7 +186,7 @@ __device__ void newton_post(const Tables &T, const NewtonState &S, const NewtonP
     for (int a = lane; a < n; a += 32)
         for (int b = 0; b <= a; ++b) S.L[(size_t)cell * npairs + tri_idx(a, b)] = H[a * n + b];
     if (lane == 0 && S.lfac) S.lfac[cell] = 1;
-    const double g = lane < n ? Ua - ua : 0.0;
+    const double g = lane < n ? fma(lane >= np.reg0 ? np.gamma : 0.0, at, Ua - ua) : 0.0;
     const double d = warp_chol_solve<n>(H, -g, lane);
     __syncwarp();
     const double gn2 = warp_sum(g * g), un2 = warp_sum(ua * ua), gd = warp_sum(g * d);

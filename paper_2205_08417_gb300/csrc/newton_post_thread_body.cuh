@@ -18,19 +18,21 @@ __device__ bool KITRT_PT_NAME(const Tables &T, const NewtonState &S, const Newto
     const int ph = S.phase[cell];
     const double lam = ph == PH_NEWTON ? S.lam[cell] : 0.0;
     double at[n], ua[n];
-    double au = 0.0;
+    double au = 0.0, ar2 = 0.0;
 KITRT_PT_UNROLL
     for (int a = 0; a < n; ++a) {
         const double al = S.alpha[off + a];
         at[a] = ph == PH_NEWTON ? fma(lam, S.dir[off + a], al) : al;
         ua[a] = u[off + a];
         au = fma(at[a], ua[a], au);
+        if (a >= np.reg0) ar2 = fma(at[a], at[a], ar2);
     }
     bool finite = true;
 KITRT_PT_UNROLL
     for (int c = 0; c < n2; ++c) finite = finite && isfinite(V[(size_t)c * vs]);
     const double fs = V[0] / T.m0;
-    const double ft = fs - au;
+    // the dual at the trial point (plus the regularization gamma/2 |alpha^r|^2)
+    const double ft = fma(0.5 * np.gamma, ar2, fs - au);
     const int ev = S.evals[cell] + 1;
     S.evals[cell] = ev;
     evals_out = ev;
@@ -77,6 +79,10 @@ KITRT_PT_UNROLL
         for (int t = T.gstart[p]; t < T.gstart[p + 1]; ++t) h = fma(T.gcoef[t], V[(size_t)T.gidx[t] * vs], h);
         Lp[p] = h;
     }
+    // regularized moments: the Hessian gains gamma on their diagonal
+KITRT_PT_UNROLL
+    for (int j = 0; j < n; ++j)
+        if (j >= np.reg0) Lp[tri_idx(j, j)] += np.gamma;
     bool spd = true;
 KITRT_PT_UNROLL
     for (int j = 0; j < n; ++j) {
@@ -117,7 +123,7 @@ KITRT_PT_UNROLL
     double gn2 = 0.0, un2 = 0.0;
 KITRT_PT_UNROLL
     for (int a = 0; a < n; ++a) {
-        const double g = V[(size_t)a * vs] - ua[a];
+        const double g = fma(a >= np.reg0 ? np.gamma : 0.0, at[a], V[(size_t)a * vs] - ua[a]);
         gn2 = fma(g, g, gn2);
         un2 = fma(ua[a], ua[a], un2);
         y[a] = -g;
@@ -140,7 +146,7 @@ KITRT_PT_UNROLL
 KITRT_PT_UNROLL
     for (int a = 0; a < n; ++a) {
         S.dir[off + a] = y[a];
-        gd = fma(V[(size_t)a * vs] - ua[a], y[a], gd);
+        gd = fma(fma(a >= np.reg0 ? np.gamma : 0.0, at[a], V[(size_t)a * vs] - ua[a]), y[a], gd);
     }
     int iters = S.iters[cell];
     if (ph == PH_NEWTON) ++iters;

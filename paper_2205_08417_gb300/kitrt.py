@@ -31,7 +31,8 @@ class Params(C.Structure):
     _fields_ = [("degree", C.c_int32), ("quad_order", C.c_int32), ("mode", C.c_int32),
                 ("bc", C.c_int32), ("tau", C.c_double), ("max_iter", C.c_int32),
                 ("max_halvings", C.c_int32), ("armijo_c1", C.c_double), ("polish", C.c_int32),
-                ("cfl", C.c_double), ("fallback_tol", C.c_double), ("order", C.c_int32)]
+                ("cfl", C.c_double), ("fallback_tol", C.c_double), ("order", C.c_int32),
+                ("reg_gamma", C.c_double), ("reg_keep_mass", C.c_int32)]
 
 
 class Stats(C.Structure):
