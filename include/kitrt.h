@@ -338,6 +338,20 @@ int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *alpha0, cons
                       int32_t nblocks, const uint8_t *target, double dt, int32_t nsteps,
                       int32_t ckpt_every, double *J, double *dJ_dsa, double *dJ_dss, void *stream);
 
+/* ---- Halo exchange of a step split over ranks [Sec. 6: the cells are split over parallel
+ * workers] ------------------------------------------------------------------------------------
+ * A rank steps its own cells plus halo layers of its neighbours' cells (a mesh built from those
+ * triangles); before each step the halo rows of u are refreshed from their owners. These two
+ * calls pack and unpack the rows (device memory, asynchronous on `stream`); the transport between
+ * ranks is the caller's (e.g. point-to-point sends). EINVAL for count < 0, width < 1 or a NULL
+ * pointer with count > 0; indices are not range-checked. */
+/* dst [count x width] row k = src row idx[k] (src [* x width] row-major, idx device int32). */
+int32_t kitrt_gather_rows(const double *src, const int32_t *idx, int32_t count, int32_t width,
+                          double *dst, void *stream);
+/* dst row idx[k] = src [count x width] row k. */
+int32_t kitrt_scatter_rows(const double *src, const int32_t *idx, int32_t count, int32_t width,
+                           double *dst, void *stream);
+
 /* ---- Learned closure [Sec. 3.1: neural entropy closures replace the Newton solve] --------------
  * A plain MLP with three softplus hidden layers maps the normalised moments v = u_{1..n-1}/u_0
  * (standardised) to alpha_{1..n-1} of the normalised problem (also standardised). Parameters are

@@ -97,6 +97,8 @@ SIGNATURES = {
     "kitrt_mn_reset": (C.c_int32, [_vp]),
     "kitrt_sn_step": (C.c_int32, [_vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, _dp, C.c_double,
                                   C.c_int32, _vp]),
+    "kitrt_gather_rows": (C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp]),
+    "kitrt_scatter_rows": (C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp]),
     "kitrt_profile_enable": (C.c_int32, [_vp, C.c_int32]),
     "kitrt_profile_read": (C.c_int32, [_vp, C.POINTER(ProfileEntry), C.c_int32, _ip]),
 }
@@ -368,6 +370,23 @@ class MNSolver:
             self.close()
         except Exception:
             pass
+
+
+# ---- Halo rows of a step split over ranks -----------------------------------------------------
+def gather_rows(src, idx, dst):
+    """dst[k] = src[idx[k]] (FP64 CUDA tensors, idx int32 CUDA)."""
+    import torch
+    _check(_lib().kitrt_gather_rows(_dev(src, torch.float64), _dev(idx, torch.int32), int(idx.numel()),
+                                    int(src.shape[1]), _dev(dst, torch.float64), _stream()),
+           "kitrt_gather_rows")
+
+
+def scatter_rows(src, idx, dst):
+    """dst[idx[k]] = src[k] (FP64 CUDA tensors, idx int32 CUDA)."""
+    import torch
+    _check(_lib().kitrt_scatter_rows(_dev(src, torch.float64), _dev(idx, torch.int32), int(idx.numel()),
+                                     int(dst.shape[1]), _dev(dst, torch.float64), _stream()),
+           "kitrt_scatter_rows")
 
 
 # ---- MLP kernels of the learned closure -------------------------------------------------------
