@@ -68,6 +68,9 @@ def parse_args():
                     help="simulated time reached by untimed set-up steps before warm-up")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sn", action="store_true", help="skip the S_N step measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the measurements beside the headline (like-for-like FP64, second "
+                         "order, regularized, adjoint, M_5)")
     ap.add_argument("--tau", type=float, default=1e-10, help="Newton tolerance of the FP64 mode")
     ap.add_argument("--tau-mixed", type=float, default=1e-8,
                     help="Newton tolerance of the mixed modes (matched to their FP32 ansatz)")
@@ -223,9 +226,9 @@ def log(msg):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
-def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None):
+def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None, **opts):
     mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
-    s = K.MNSolver(mesh, W["N"], W["order"], mode=mode, tau=tau)
+    s = K.MNSolver(mesh, W["N"], W["order"], mode=mode, tau=tau, **opts)
     if net is not None:
         s.set_mlp(net.params, net.norm)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -325,6 +328,137 @@ def run_sn(K, torch, W, steps, warmup, fp32, hbm_peak, workload):
     return out
 
 
+def flux_roofline(W, work_n, Qf, prof, hbm_peak, fp32=True):
+    """HBM roofline of the flux kernel: algorithmic bytes per cell = the cell's own ansatz row
+    (Q' b; the three upwind rows are other cells' rows and count once), u read and written
+    (16 n), neighbours (16), normals and inverse area (28 FP32 / 56 FP64), sigma_a, sigma_s, q
+    (24)."""
+    pf = prof.get("flux_update")
+    if not pf:
+        return None
+    b = 4 if fp32 else 8
+    per_cell = Qf * b + 16 * work_n + 16 + (28 if fp32 else 56) + 24
+    launch_ms = pf["total_ms"] / pf["launches"]
+    gbs = W["C"] * per_cell / (launch_ms / 1e3) / 1e9
+    return {"kernel": "flux_update", "bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+            "unit": "GB/s", "frac": gbs / hbm_peak, "bytes_per_cell": per_cell,
+            "avg_launch_ms": launch_ms, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
+def mode_line(W, r, steps):
+    line = {"ms_per_step": r["ms"] / steps, "cell_updates_per_s": W["C"] * steps / (r["ms"] / 1e3),
+            "evaluations_per_cell_step": r["stats"]["evaluations"] / (W["C"] * steps),
+            "kernels_ms_per_step": {k: v["total_ms"] / steps for k, v in r["prof"].items()}}
+    st = r["stats"]
+    if st.get("proposals"):
+        line["network_proposals_per_cell_step"] = st["proposals"] / (W["C"] * steps)
+        line["network_accept_rate"] = 1.0 - st["fallbacks"] / st["proposals"]
+        line["fallbacks_per_cell_step"] = st["fallbacks"] / (W["C"] * steps)
+    return line
+
+
+def sweep_roofline(r, work, peak):
+    key = "closure_eval_fp64" if r["mode"] == "fp64" else "closure_eval_mixed"
+    pe = r["prof"].get(key)
+    if not pe or pe["total_ms"] <= 0:
+        return None
+    t = pe["total_ms"] / 1e3
+    out = {"kernel": key, "fp64_ops_per_cell_eval": work["sweep_fp64_ops"],
+           "fp64_pipe_frac": pe["units"] * work["sweep_fp64_ops"] / t / 1e12 / (peak / 2.0),
+           "cell_evals": pe["units"]}
+    if work["tensor_flops"]:
+        out["tensor_tflops"] = pe["units"] * work["tensor_flops"] / t / 1e12
+    return out
+
+
+def run_extras(K, torch, args, peak, hbm_peak, head_results):
+    """Untimed-region measurements beside the headline (each timed the same way: CUDA events
+    around K steps after warm-up): the like-for-like FP64 line, the second-order and regularized
+    steps on the same workload, the adjoint configuration's gradient, and the large M_5
+    configuration in every mode."""
+    ex = {}
+    W = make_workload(args.workload)
+    steps = min(args.steps, 10)
+    ref_u0 = head_results["fp64"]["u"][:, 0] if "fp64" in head_results else None
+
+    def err(r):
+        if ref_u0 is None:
+            return None
+        return float(np.linalg.norm(r["u"][:, 0] - ref_u0) / np.linalg.norm(ref_u0))
+
+    r = run_mode(K, torch, W, "fp64", steps, args.warmup, args.t_start, args.tau_mixed, e2e=False)
+    ex["d2_fp64_tau_like_mixed"] = dict(mode_line(W, r, steps), tau=args.tau_mixed,
+                                        u0_rel_l2_vs_fp64=err(r))
+    log(f"extra fp64 tau {args.tau_mixed}: {r['ms'] / steps:.3f} ms/step")
+    for mode in ("mixed_tf32", "fp64"):
+        r = run_mode(K, torch, W, mode, steps, args.warmup, args.t_start,
+                     args.tau if mode == "fp64" else args.tau_mixed, e2e=False, order=2)
+        ex[f"d2_second_order_{mode}"] = mode_line(W, r, steps)
+        ex[f"d2_second_order_{mode}"]["u"] = r["u"]
+        log(f"extra second order {mode}: {r['ms'] / steps:.3f} ms/step")
+    a, b = ex["d2_second_order_mixed_tf32"].pop("u"), ex["d2_second_order_fp64"].pop("u")
+    ex["d2_second_order_mixed_tf32"]["u0_rel_l2_vs_fp64"] = float(
+        np.linalg.norm(a[:, 0] - b[:, 0]) / np.linalg.norm(b[:, 0]))
+    r = run_mode(K, torch, W, "mixed_tf32", steps, args.warmup, args.t_start, args.tau_mixed,
+                 e2e=False, reg_gamma=1e-3)
+    ex["d2_regularized_mixed_tf32"] = dict(mode_line(W, r, steps), reg_gamma=1e-3, reg_keep_mass=1)
+    log(f"extra regularized: {r['ms'] / steps:.3f} ms/step")
+
+    # adjoint configuration: 7x7 block medium on [0,7]^2, M_3, order 10, 400 steps, checkpoints
+    # every 16, absorbed energy of the centre 3x3 blocks and its 98 gradients
+    from paper_2205_08417_gb300 import synth
+    spec = synth.WORKLOADS["m3_blocks_60k"]
+    m = synth.jittered_mesh(spec["k"], spec["lo"], spec["hi"], spec["seed"])
+    cen = m.centroids()
+    blk, sab, ssb = synth.block_coefficients(cen, 0.0, 7.0, 7, spec["seed"])
+    bx, by = blk // 7, blk % 7
+    tgt = ((bx >= 2) & (bx <= 4) & (by >= 2) & (by <= 4)).astype(np.uint8)
+    q = np.where(blk == 24, 1.0, 0.0)
+    n3 = (spec["N"] + 1) * (spec["N"] + 2) // 2
+    u0 = np.zeros((m.ncells, n3))
+    u0[:, 0] = 1e-4 / math.sqrt(4 * math.pi)
+    mesh = K.Mesh(m.xy, m.tri)
+    s = K.MNSolver(mesh, spec["N"], spec["order"], bc="vacuum", tau=1e-12)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    ud = d(u0)
+    ad = s.isotropic_alpha(ud)
+    args3 = (ud, ad, d(sab[blk]), d(ssb[blk]), d(q), d(blk.astype(np.int32)), 49, d(tgt),
+             0.4 * mesh.geometry()["min_inradius"], 400, 16)
+    s.adjoint(*args3)  # warm-up (allocates the checkpoint workspace)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, gsa, gss = s.adjoint(*args3)
+    el = time.perf_counter() - t0
+    ex["d3_adjoint"] = {"cells": m.ncells, "steps": 400, "ckpt_every": 16, "coefficients": 98,
+                        "seconds_per_gradient": el, "J": J,
+                        "cell_steps_per_s_forward_and_reverse": m.ncells * 400 / el}
+    log(f"extra adjoint: {el:.3f} s per gradient")
+
+    # large M_5 configuration: ~1M triangles, block medium, a few steps after t = 0.01 in each mode
+    W5 = make_workload("m5_line_source_1m")
+    net5 = train_network(K, torch, W5, 500_000)
+    d5 = {"cells": W5["C"], "nmom": W5["n"], "quad_points": 2 * W5["order"] ** 2, "modes": {}}
+    res5 = {}
+    for mode, tau in (("mixed_tf32", args.tau_mixed), ("fp64", args.tau), ("learned", args.tau_mixed)):
+        r = run_mode(K, torch, W5, mode, 5, 2, 0.01, tau, e2e=False,
+                     net=net5 if mode == "learned" else None)
+        res5[mode] = r
+        line = mode_line(W5, r, 5)
+        line["sweep"] = sweep_roofline(r, r["solver"].work(), peak)
+        line["flux"] = flux_roofline(W5, W5["n"], W5["order"] ** 2, r["prof"], hbm_peak,
+                                     fp32=mode != "fp64")
+        d5["modes"][mode] = line
+        log(f"extra M_5 {mode}: {r['ms'] / 5:.1f} ms/step")
+    ref5 = res5["fp64"]["u"][:, 0]
+    for mode in ("mixed_tf32", "learned"):
+        d5["modes"][mode]["u0_rel_l2_vs_fp64"] = float(
+            np.linalg.norm(res5[mode]["u"][:, 0] - ref5) / np.linalg.norm(ref5))
+    d5["learned_training"] = net5.info
+    ex["d5_m5_blocks_1m"] = d5
+    return ex
+
+
 def hbm_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -404,6 +538,9 @@ def main():
         hp = hbm_peak_gbs()
         sn = {"sn_fp32": run_sn(K, torch, W, args.steps, args.warmup, True, hp, args.workload),
               "sn_fp64": run_sn(K, torch, W, args.steps, args.warmup, False, hp, args.workload)}
+    extras = None
+    if not args.no_extras and world == 1:
+        extras = run_extras(K, torch, args, peak, hbm_peak_gbs(), results)
     head = results[args.mode]
     if world > 1:
         ms, e2e_ms = max_over_ranks([head["ms"], head.get("e2e_ms", float("nan"))], "cuda")
@@ -485,11 +622,10 @@ def main():
                         "share": v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in head["prof"].values()))}
                     for k, v in head["prof"].items()},
         "learned_training": None if net is None else net.info,
-        "modes": {m: {"cell_updates_per_s": C * args.steps / (r["ms"] / 1e3), "tau": r["tau"],
-                      "fallbacks_per_cell_step": r["stats"]["fallbacks"] / (C * args.steps),
-                      "ms_per_step": r["ms"] / args.steps,
-                      "evaluations_per_cell_step": r["stats"]["evaluations"] / (C * args.steps)}
-                  for m, r in results.items()},
+        "modes": {m: dict(mode_line(W, r, args.steps), tau=r["tau"]) for m, r in results.items()},
+        "flux_roofline": flux_roofline(W, n, Qf, head["prof"], hbm_peak_gbs(),
+                                       fp32=args.mode != "fp64"),
+        "extras": extras,
         "error": errors,
         "sn": sn,
         "e2e": None if args.no_e2e else {

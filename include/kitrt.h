@@ -109,6 +109,8 @@ typedef struct {
     int64_t launches;      /* CUDA kernels the library launched in this call */
     int64_t restarts;      /* KITRT_LEARNED: fallbacks whose better start was the previous closure's
                               point, stepped from its stored Cholesky factor without a new pass */
+    int64_t proposals;     /* KITRT_LEARNED: closures the network was asked for (the rest were
+                              already converged from the previous step's state) */
 } kitrt_stats;
 
 /* Per-kernel-kind trace record (see kitrt_profile_enable). `units` counts what one kind

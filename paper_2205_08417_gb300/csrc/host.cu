@@ -854,21 +854,24 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
             if (!rc) rc = launch_post(mn, T, mn->st, C, u, k, np, mn->d_Vacc, s);
             if (rc) return rc;
         }
-        CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 10 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 11 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CUDA_OK(cudaStreamSynchronize(s));
         if (mn->h_cnt[7]) return mn->h_cnt[7];
         int active = mn->h_cnt[k % 3];
         if (active == 0) break;
         if (k >= max_launch) return KITRT_ETIMEOUT;
     }
+    // the sweeps' evaluations (the network's residual passes run in their own kernel)
     if (mn->prof_on) mn->prof_units[mn->p.mode == KITRT_FP64 ? PK_EVAL : PK_EVAL_MIXED] += mn->h_cnt[6];
+    if (mn->prof_on && mn->p.mode == KITRT_LEARNED) mn->prof_units[PK_MLP] += mn->h_cnt[10];
     if (stats) {
         stats->closures += C;
-        stats->evaluations += mn->h_cnt[6];
+        stats->evaluations += mn->h_cnt[6] + mn->h_cnt[10];
         stats->max_evals = std::max(stats->max_evals, mn->h_cnt[4]);
         stats->failed = mn->h_cnt[3];
         stats->fallbacks += mn->h_cnt[5];
         stats->restarts += mn->h_cnt[9];
+        if (mn->p.mode == KITRT_LEARNED) stats->proposals += mn->h_cnt[8];
     }
     if (mn->h_cnt[3] > 0) {
         // report the first failing code

@@ -86,7 +86,8 @@ struct NewtonState {
     int32_t *cnt;      // [16]: cnt[0..2] rotating list counters, cnt[3] failures, cnt[4] max
                        //   evals, cnt[5] fallbacks, cnt[6] evaluations, cnt[7] timeout status,
                        //   cnt[8] predictor list length, cnt[9] learned-mode steps taken
-                       //   from a stored factor
+                       //   from a stored factor, cnt[10] learned-mode residual passes of the
+                       //   network's proposals
 };
 
 struct NewtonParams {

@@ -67,7 +67,7 @@ learned_pass_kernel(Tables T, NewtonState S, const double *__restrict__ u,
         const double r2 = warp_sum(r * r), un2 = warp_sum(ua * ua);
         // dual objective of the network's point: <exp(alpha.m)> = u_0 / m_0 after the mass fix
         const double f_nn = u0 / T.m0 - (alpha0 * u0 + warp_sum(al * ua));
-        if (lane == 0) atomicAdd(&S.cnt[6], 1);  // a quadrature pass of this cell
+        if (lane == 0) atomicAdd(&S.cnt[10], 1);  // a quadrature pass of this cell (the network's)
         const bool finite = isfinite(alpha0) && isfinite(r2) && isfinite(f_nn) && u0 > 0.0;
         const bool ok = finite && r2 <= tol * tol * un2;
         if (ok) {

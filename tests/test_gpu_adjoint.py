@@ -4,6 +4,7 @@ and through the torch.autograd binding. Checkerboard-like block media (Sec. 7.2)
 sigma_a in [0,10], sigma_s in [0,1], unit isotropic source in the centre block, vacuum walls,
 absorbed energy in the centre 3x3 blocks."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -64,6 +65,27 @@ def test_adjoint_matches_oracle_adjoint(K, ckpt):
     assert abs(J - Jo) <= 1e-12 * abs(Jo)
     g, go = np.concatenate([gsa, gss]), np.concatenate([gsao, gsso])
     assert np.linalg.norm(g - go) / np.linalg.norm(go) <= 1e-9
+
+
+def test_adjoint_m3_order10_matches_oracle_adjoint(K):
+    """The adjoint configuration's arithmetic at a size the oracle handles: M_3, order 10, a
+    31^2-point mesh of the 7x7 block medium, 32 steps with checkpoints every 16 (two segments, the
+    recomputation path): J to 1e-12 and the 98 gradients to 1e-9 relative L2 of the oracle's
+    exact transpose."""
+    N, order, nsteps, ckpt = 3, 10, 32, 16
+    m, mesh, blk, sa, ss, q, tgt, u0 = blocks_problem(K, 31, N, order)
+    s = K.MNSolver(mesh, N, order, bc="vacuum", tau=1e-13)
+    G = O.Geometry(m.xy, m.tri)
+    T = O.Tables(N, order)
+    dt = G.cfl_dt(0.4)
+    J, gsa, gss = gpu_J_grad(K, s, blk, sa, ss, q, tgt, u0, dt, nsteps, ckpt)
+    Jo, gsao, gsso = O.mn_adjoint(T, G, blk.astype(np.int32), sa, ss, q, tgt, dt, nsteps, u0,
+                                  O.isotropic_alpha(T, u0), bc=1, tau=1e-13)
+    assert abs(J - Jo) <= 1e-12 * abs(Jo)
+    g, go = np.concatenate([gsa, gss]), np.concatenate([gsao, gsso])
+    err = np.linalg.norm(g - go) / np.linalg.norm(go)
+    print("M_3 order 10 adjoint vs oracle: rel L2", err)
+    assert err <= 1e-9
 
 
 def test_adjoint_matches_central_differences(K):
@@ -129,3 +151,31 @@ def test_adjoint_full_size_blocks_sampled_fd(K):
         Jm = gpu_J_grad(K, s, blk, pm[:49], pm[49:], q, tgt, u0, dt, nsteps, nsteps)[0]
         fd = (Jp - Jm) / (2 * h)
         assert abs(fd - g[k]) <= 1e-6 * scale, (k, fd, g[k], scale)
+
+
+@pytest.mark.skipif(os.environ.get("KITRT_EVIDENCE_FD") != "1",
+                    reason="evidence run (about 3 minutes): set KITRT_EVIDENCE_FD=1")
+def test_adjoint_full_size_all_98_coefficients_fd(K):
+    """The adjoint configuration at full size (~60k triangles, M_3, order 10, 400 steps,
+    checkpoints every 16) against central differences (h = 1e-6) of every one of the 98
+    coefficients: |FD - adjoint| <= 1e-6 max |gradient| (196 forward runs)."""
+    N, order, nsteps, h = 3, 10, 400, 1e-6
+    m, mesh, blk, sa, ss, q, tgt, u0 = blocks_problem(K, 173, N, order)
+    s = K.MNSolver(mesh, N, order, bc="vacuum", tau=1e-12)
+    dt = 0.4 * mesh.geometry()["min_inradius"]
+    J, gsa, gss = gpu_J_grad(K, s, blk, sa, ss, q, tgt, u0, dt, nsteps, 16)
+    g = np.concatenate([gsa, gss])
+    scale = np.abs(g).max()
+    p0 = np.concatenate([sa, ss])
+    fd = np.zeros_like(g)
+    for k in range(g.size):
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        Jp = gpu_J_grad(K, s, blk, pp[:49], pp[49:], q, tgt, u0, dt, nsteps, nsteps)[0]
+        Jm = gpu_J_grad(K, s, blk, pm[:49], pm[49:], q, tgt, u0, dt, nsteps, nsteps)[0]
+        fd[k] = (Jp - Jm) / (2 * h)
+    err = np.abs(fd - g) / scale
+    print("full-size adjoint vs FD over 98 coefficients: max", err.max(), "median", np.median(err),
+          "J", J)
+    assert err.max() <= 1e-6
