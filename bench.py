@@ -387,10 +387,12 @@ def run_extras(K, torch, args, peak, hbm_peak, head_results):
             return None
         return float(np.linalg.norm(r["u"][:, 0] - ref_u0) / np.linalg.norm(ref_u0))
 
-    r = run_mode(K, torch, W, "fp64", steps, args.warmup, args.t_start, args.tau_mixed, e2e=False)
-    ex["d2_fp64_tau_like_mixed"] = dict(mode_line(W, r, steps), tau=args.tau_mixed,
+    # same step count as the headline FP64 run, so that both states are at the same time
+    r = run_mode(K, torch, W, "fp64", args.steps, args.warmup, args.t_start, args.tau_mixed,
+                 e2e=False)
+    ex["d2_fp64_tau_like_mixed"] = dict(mode_line(W, r, args.steps), tau=args.tau_mixed,
                                         u0_rel_l2_vs_fp64=err(r))
-    log(f"extra fp64 tau {args.tau_mixed}: {r['ms'] / steps:.3f} ms/step")
+    log(f"extra fp64 tau {args.tau_mixed}: {r['ms'] / args.steps:.3f} ms/step")
     for mode in ("mixed_tf32", "fp64"):
         r = run_mode(K, torch, W, mode, steps, args.warmup, args.t_start,
                      args.tau if mode == "fp64" else args.tau_mixed, e2e=False, order=2)

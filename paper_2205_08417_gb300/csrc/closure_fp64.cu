@@ -558,10 +558,15 @@ int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, cons
     // small blocks spread them over every SM instead of a few
     int blocks = (C + kPostBlock - 1) / kPostBlock;
     if (blocks > mn->nsm * 32) blocks = mn->nsm * 32;
-    LaunchScope ls(mn, PK_POST, s, 0);
     const int mixed = mn->p.mode != KITRT_FP64;
     const int target = mixed ? mn->target_mixed : mn->target_fp64;
-    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, kPostBlock, 0, s>>>(T, S, u, k, np, Vacc, mn->vs, mixed, target));
+    const size_t smem = post_smem_bytes(mn->n, mn->n2, mn->npairs, mn->gaunt_nnz, mixed != 0,
+                                        kUnrolledNewton && mn->N <= 3);
+    int rc = KITRT_OK;
+    KITRT_DISPATCH_N(mn->N, rc = ensure_dyn_smem(post_thread_kernel<NN>, smem));
+    if (rc) return rc;
+    LaunchScope ls(mn, PK_POST, s, 0);
+    KITRT_DISPATCH_N(mn->N, post_thread_kernel<NN><<<blocks > 0 ? blocks : 1, kPostBlock, smem, s>>>(T, S, u, k, np, Vacc, mn->vs, mixed, target, mn->gaunt_nnz));
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 

@@ -1,7 +1,7 @@
 // Kinetic upwind flux of the closed ansatz and the explicit first-order update
 // [Sec. 4.4 kinetic numerical flux; Sec. 4.2 explicit iteration; Sec. 3.1 isotropic scattering].
 //
-// Cell-centric gather: one warp per cell i, lanes over the folded quadrature points. The upwind
+// Cell-centric gather (lanes over the folded quadrature points of a cell). The upwind
 // flux sum_f sum_q w_q m_q (Omega_q.n_f) psi_up is evaluated in its fluctuation form
 //     F_i = sum_f sum_{q: Omega_q.n_f < 0} w_q m_q (Omega_q.n_f) (psi_up,f,q - psi_iq),
 // which equals it exactly in exact arithmetic because the scaled normals of a closed cell sum to
@@ -18,58 +18,102 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 8;
-constexpr int kBatch = 4;     // cells per warp batch in the FP32 flux
-constexpr int kTogether = 2;  // cells of a batch whose points one pass over the tables serves
 
-template <int NN, typename PsiT>
+// Slots of a reduce-scatter of n sums: the next power of two >= n, and its log2.
+template <int n>
+struct Slots {
+    static constexpr int S = n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+    static constexpr int H = S == 1 ? 0 : S == 2 ? 1 : S == 4 ? 2 : S == 8 ? 3 : S == 16 ? 4 : 5;
+};
+
+// Plain FP64 reduce-scatter of n per-lane sums across the warp: at each of log2(S) halving levels
+// (offsets 16, 8, ...) a lane keeps one half of its slots and adds its partner's copy of that half;
+// the remaining levels are butterflies between lanes holding the same slot. Lane L ends with the
+// total of slot L >> (5 - H): S - 1 + 5 - H additions per lane instead of 5 n for a butterfly per
+// sum (each one a warp-wide FP64 instruction).
+template <int n>
+__device__ __forceinline__ double warp_reduce_scatter64(const double (&F)[n], int lane)
+{
+    constexpr int S = Slots<n>::S, H = Slots<n>::H;
+    double sv[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) sv[k] = k < n ? F[k < n ? k : 0] : 0.0;
+#pragma unroll
+    for (int lvl = 0; lvl < H; ++lvl) {
+        const int o = 16 >> lvl;
+        const int half = S >> (lvl + 1);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const double keep = upper ? sv[k + half] : sv[k];
+            const double give = upper ? sv[k] : sv[k + half];
+            sv[k] = keep + __shfl_xor_sync(kFull, give, o);
+        }
+    }
+    double r = sv[0];
+#pragma unroll
+    for (int o = 16 >> H; o > 0; o >>= 1) r += __shfl_xor_sync(kFull, r, o);
+    return r;
+}
+
+// FP64 flux (FP64 mode): one warp per cell, lanes over the points. The FP64 pipe is the bound
+// (a warp-wide FP64 instruction occupies it for 16 cycles), so the inflow test reads the sign
+// bit of Omega.n in integer arithmetic instead of comparing in FP64, and the moments are reduced
+// with a reduce-scatter.
+// RHO: the transformed CSD equation's density (Sec. 2, Eq. BoltzmannCSDTrafo): the transported
+// value is psi / rho, so each row is scaled by its cell's 1/rho (invrho) before differencing.
+template <int NN, bool RHO>
 __global__ void __launch_bounds__(kWarps * 32)
 flux_update_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restrict__ nrm,
-                   const double *__restrict__ area, const PsiT *__restrict__ psi,
-                   double *__restrict__ u, const double *__restrict__ sa,
-                   const double *__restrict__ ss, const double *__restrict__ qs, double dt,
-                   int bc, int C)
+                   const double *__restrict__ area, const double *__restrict__ psi,
+                   const double *__restrict__ invrho, double *__restrict__ u,
+                   const double *__restrict__ sa, const double *__restrict__ ss,
+                   const double *__restrict__ qs, double dt, int bc, int C)
 {
     constexpr int n = (NN + 1) * (NN + 2) / 2;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int Qp = T.Qp;
     for (int i = blockIdx.x * kWarps + wib; i < C; i += gridDim.x * kWarps) {
         const int4 nb = nbr[i];
-        const double nx0 = nrm[6 * (size_t)i], ny0 = nrm[6 * (size_t)i + 1];
-        const double nx1 = nrm[6 * (size_t)i + 2], ny1 = nrm[6 * (size_t)i + 3];
-        const double nx2 = nrm[6 * (size_t)i + 4], ny2 = nrm[6 * (size_t)i + 5];
-        const PsiT *pi_row = psi + (size_t)i * Qp;
+        const int nbf[3] = {nb.x, nb.y, nb.z};
+        double nx[3], ny[3], g[3];
+        const double *up[3];
+        const double *own = psi + (size_t)i * Qp;
+        const double ri = RHO ? invrho[i] : 1.0;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            nx[f] = nrm[6 * (size_t)i + 2 * f];
+            ny[f] = nrm[6 * (size_t)i + 2 * f + 1];
+            // upwind row: the neighbour's, or the cell's own as the ghost (Neumann: fluctuation
+            // 0; vacuum: scaled by 0, so the fluctuation is -psi_i)
+            up[f] = nbf[f] >= 0 ? psi + (size_t)nbf[f] * Qp : own;
+            g[f] = (nbf[f] >= 0 || bc == 0) ? 1.0 : 0.0;
+            if (RHO) {
+                g[f] *= nbf[f] >= 0 ? invrho[nbf[f]] : ri;
+                // Neumann ghost: its fluctuation is exactly zero, so the face drops out (the
+                // scaled difference ri psi_i - ri psi_i would leave a rounding residue)
+                if (nbf[f] < 0 && bc == 0) nx[f] = ny[f] = 0.0;
+            }
+        }
         double F[n];
 #pragma unroll
         for (int a = 0; a < n; ++a) F[a] = 0.0;
         for (int q = lane; q < Qp; q += 32) {
-            const double pi = (double)pi_row[q];
+            const double pi = RHO ? ri * own[q] : own[q];
             const double wx = T.wox[q], wy = T.woy[q];
-            const double ghost = bc == 0 ? pi : 0.0;
             double s = 0.0;
-            {
-                const double d = fma(wx, nx0, wy * ny0);
-                if (d < 0.0) s = fma(d, (nb.x >= 0 ? (double)psi[(size_t)nb.x * Qp + q] : ghost) - pi, s);
-            }
-            {
-                const double d = fma(wx, nx1, wy * ny1);
-                if (d < 0.0) s = fma(d, (nb.y >= 0 ? (double)psi[(size_t)nb.y * Qp + q] : ghost) - pi, s);
-            }
-            {
-                const double d = fma(wx, nx2, wy * ny2);
-                if (d < 0.0) s = fma(d, (nb.z >= 0 ? (double)psi[(size_t)nb.z * Qp + q] : ghost) - pi, s);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const double d = fma(wx, nx[f], wy * ny[f]);
+                const double dm = __double2hiint(d) < 0 ? d : 0.0;  // min(d, 0); -0 adds nothing
+                s = fma(dm, fma(g[f], up[f][q], -pi), s);
             }
 #pragma unroll
             for (int a = 0; a < n; ++a) F[a] = fma(T.Mt[a * Qp + q], s, F[a]);
         }
-#pragma unroll
-        for (int a = 0; a < n; ++a) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) F[a] += __shfl_xor_sync(kFull, F[a], o);
-        }
-        double Fa = 0.0;
-#pragma unroll
-        for (int a = 0; a < n; ++a)
-            if (lane == a) Fa = F[a];
+        const double r = warp_reduce_scatter64<n>(F, lane);
+        // slot a is held by lane a << (5 - H)
+        const double Fa = __shfl_sync(kFull, r, (lane << (5 - Slots<n>::H)) & 31);
         const double u0 = u[(size_t)i * n];
         if (lane < n) {
             const double ua = u[(size_t)i * n + lane];
@@ -79,11 +123,22 @@ flux_update_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restr
     }
 }
 
-// FP32 variant for the mixed modes: FP32 ansatz and upwind sums, Kahan-compensated FP32
-// projection per lane, a compensated (two-sum) FP32 reduce-scatter across the warp, and the FP64
-// update applied afterwards with every lane busy. A warp takes a batch of kBatch consecutive cells:
-// their flux moments go to shared memory, then the warp updates all (cell, moment) pairs of the
-// batch (FP64 instructions on a partly idle warp cost as much as on a full one).
+// FP32 flux of the mixed modes. FP64 instructions are rare on this GPU (2 per clock per SM), so
+// none is spent on warp-uniform values: normals and inverse areas come from the mesh's FP32
+// copies, the per-cell coefficients are converted by different lanes at once, and the update
+// increment dt (-F/A + R(u)) is formed in FP32; only u += increment is FP64 (lanes over the
+// (cell, moment) elements of a warp's cells).
+//
+// Layout of the work: a group of kGroup = 8 lanes per cell, 4 cells per warp. Each lane reads
+// 16-byte pieces (4 consecutive points) of the cell's row and of its three upwind rows, and the
+// matching pieces of the tables, which the warp's 4 cells read at the same addresses (one
+// request serves them). Q' padded to a multiple of 32 gives every lane the same number of pieces.
+// Each lane sums its points in plain FP32; the 8 lane sums of a cell are reduced with a
+// compensated (two-sum) reduce-scatter.
+constexpr int kGroup = 8;
+constexpr int kCellsPerWarp = 32 / kGroup;
+constexpr int kGroupLog = 3;
+
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
     s = a + b;
@@ -91,30 +146,35 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - (s - bp)) + (b - bp);
 }
 
-// Compensated reduce-scatter of n per-lane sums (F - Fc) across the warp. The sums are padded to
-// S slots (the next power of two >= n). At each of the log2(S) halving levels (offsets 16, 8, ...)
-// a lane keeps one half of its slots, sends the other half to its partner and adds the partner's
-// copy of the kept half with a two-sum; the remaining levels are compensated butterflies between
-// lanes holding the same slot. Lane L ends with the total of slot L >> (5 - log2 S) (value s + e);
-// every lane whose low 5 - log2 S bits are zero holds a distinct slot. That is S - 1 two-sums per
-// lane (plus 5 - log2 S for the butterflies) instead of 5 n for a butterfly per sum.
+// Compensated reduce-scatter of n per-lane sums over a group of G = 2^kGroupLog lanes. Halving
+// levels with offsets G/2, G/4, ... (at most log2 G of them) leave each lane K = S >> H of the
+// padded S slots; the remaining levels are compensated butterflies between lanes holding the same
+// slots. Lane gl of the group ends with slots base .. base + K - 1, base = (gl >> (log2 G - H)) K,
+// values rs[k] + re[k]; it returns whether it is the unique holder of them.
 template <int n>
-__device__ __forceinline__ int warp_reduce_scatter(const float (&F)[n], const float (&Fc)[n], int lane,
-                                                   float &rs, float &re)
+struct GroupRS {
+    static constexpr int S = Slots<n>::S;
+    static constexpr int H = Slots<n>::H < kGroupLog ? Slots<n>::H : kGroupLog;
+    static constexpr int K = S >> H;
+};
+
+template <int n>
+__device__ __forceinline__ bool group_reduce_scatter(const float (&F)[n], int gl,
+                                                     float (&rs)[GroupRS<n>::K],
+                                                     float (&re)[GroupRS<n>::K], int &base)
 {
-    constexpr int S = n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
-    constexpr int H = S == 1 ? 0 : S == 2 ? 1 : S == 4 ? 2 : S == 8 ? 3 : S == 16 ? 4 : 5;
+    constexpr int S = GroupRS<n>::S, H = GroupRS<n>::H, K = GroupRS<n>::K;
     float sv[S], ev[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         sv[k] = k < n ? F[k < n ? k : 0] : 0.0f;
-        ev[k] = k < n ? -Fc[k < n ? k : 0] : 0.0f;
+        ev[k] = 0.0f;
     }
 #pragma unroll
     for (int lvl = 0; lvl < H; ++lvl) {
-        const int o = 16 >> lvl;
+        const int o = (1 << (kGroupLog - 1)) >> lvl;
         const int half = S >> (lvl + 1);
-        const bool upper = (lane & o) != 0;
+        const bool upper = (gl & o) != 0;
 #pragma unroll
         for (int k = 0; k < half; ++k) {
             const float ks = upper ? sv[k + half] : sv[k], ke = upper ? ev[k + half] : ev[k];
@@ -126,118 +186,128 @@ __device__ __forceinline__ int warp_reduce_scatter(const float (&F)[n], const fl
             ev[k] = ke + pe + e;
         }
     }
-    float s0 = sv[0], e0 = ev[0];
 #pragma unroll
-    for (int o = 16 >> H; o > 0; o >>= 1) {
-        const float so = __shfl_xor_sync(kFull, s0, o), eo = __shfl_xor_sync(kFull, e0, o);
-        float t, e;
-        two_sum(s0, so, t, e);
-        s0 = t;
-        e0 = e0 + eo + e;
+    for (int k = 0; k < K; ++k) {
+        float s0 = sv[k], e0 = ev[k];
+#pragma unroll
+        for (int o = (1 << (kGroupLog - 1)) >> H; o > 0; o >>= 1) {
+            const float so = __shfl_xor_sync(kFull, s0, o), eo = __shfl_xor_sync(kFull, e0, o);
+            float t, e;
+            two_sum(s0, so, t, e);
+            s0 = t;
+            e0 = e0 + eo + e;
+        }
+        rs[k] = s0;
+        re[k] = e0;
     }
-    rs = s0;
-    re = e0;
-    // the lane's slot, or -1 for a lane that only duplicates another's slot
-    return (lane & ((1 << (5 - H)) - 1)) == 0 ? lane >> (5 - H) : -1;
+    base = (gl >> (kGroupLog - H)) * K;
+    return (gl & ((1 << (kGroupLog - H)) - 1)) == 0;
 }
 
-// The FP32 flux of the mixed modes. FP64 instructions are rare on this GPU (2 per clock per SM), so
-// none is spent on warp-uniform values: normals and inverse areas come from the mesh's FP32
-// copies, the per-cell coefficients are converted by different lanes at once, and the update
-// increment dt (-F/A + R(u)) is formed in FP32; only u += increment is FP64 (lanes over the
-// (cell, moment) elements of a batch). Each lane sums its ~Q'/32 points in plain FP32; the warp
-// reduction of the 32 lane sums is compensated.
-template <int NN>
-__global__ void __launch_bounds__(kWarps * 32)
+// Upwind fluctuation sum of one point: s = sum_f min(Omega.n_f, 0) (psi_up,f - psi_i), or with a
+// density (RHO) sum_f min(Omega.n_f, 0) (psi_up,f / rho_up,f - psi_i / rho_i) (r: the 1/rho).
+template <bool RHO>
+__device__ __forceinline__ float point_fluct(float wx, float wy, const float (&nx)[3],
+                                             const float (&ny)[3], float ri, const float (&r)[3],
+                                             float pi, float u0, float u1, float u2)
+{
+    if (RHO) {
+        const float tp = ri * pi;
+        float s = fminf(fmaf(wx, nx[0], wy * ny[0]), 0.0f) * fmaf(r[0], u0, -tp);
+        s = fmaf(fminf(fmaf(wx, nx[1], wy * ny[1]), 0.0f), fmaf(r[1], u1, -tp), s);
+        return fmaf(fminf(fmaf(wx, nx[2], wy * ny[2]), 0.0f), fmaf(r[2], u2, -tp), s);
+    }
+    float s = fminf(fmaf(wx, nx[0], wy * ny[0]), 0.0f) * (u0 - pi);
+    s = fmaf(fminf(fmaf(wx, nx[1], wy * ny[1]), 0.0f), u1 - pi, s);
+    return fmaf(fminf(fmaf(wx, nx[2], wy * ny[2]), 0.0f), u2 - pi, s);
+}
+
+// Latency bound: 3 resident blocks per SM (at most 85 registers) measured 0.127 ms per M_3 launch
+// on 99,458 cells against 0.179 ms at the unconstrained 94 registers (2 blocks).
+template <int NN, bool RHO>
+__global__ void __launch_bounds__(kWarps * 32, NN <= 3 ? 3 : 2)
 flux_update32_kernel(Tables T, const int4 *__restrict__ nbr, const float *__restrict__ nrm32,
                      const float *__restrict__ inva32, const float *__restrict__ psi,
-                     double *__restrict__ u, const double *__restrict__ sa,
-                     const double *__restrict__ ss, const double *__restrict__ qs, float dt,
-                     int bc, int C)
+                     const float *__restrict__ zrow, const float *__restrict__ invrho32,
+                     double *__restrict__ u,
+                     const double *__restrict__ sa, const double *__restrict__ ss,
+                     const double *__restrict__ qs, float dt, int bc, int C)
 {
     constexpr int n = (NN + 1) * (NN + 2) / 2;
-    __shared__ float sF[kWarps][kBatch * n];
-    __shared__ float sK[kWarps][kBatch][4];  // per cell: sigma_a, sigma_s, q, 1/A (FP32)
+    constexpr int K = GroupRS<n>::K;
+    __shared__ float sF[kWarps][kCellsPerWarp * n];
+    __shared__ float sK[kWarps][kCellsPerWarp][4];  // per cell: sigma_a, sigma_s, q, 1/A (FP32)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int Qp = T.Qp;
-    for (int base = (blockIdx.x * kWarps + wib) * kBatch; base < C; base += gridDim.x * kWarps * kBatch) {
-        const int nb_cells = C - base < kBatch ? C - base : kBatch;
+    const int grp = lane >> kGroupLog, gl = lane & (kGroup - 1);
+    const int Qp = T.Qp, nq4 = Qp / 4;
+    const float4 *__restrict__ wx4 = reinterpret_cast<const float4 *>(T.wox32);
+    const float4 *__restrict__ wy4 = reinterpret_cast<const float4 *>(T.woy32);
+    const float4 *__restrict__ M4 = reinterpret_cast<const float4 *>(T.Mt32);
+    for (int base = (blockIdx.x * kWarps + wib) * kCellsPerWarp; base < C;
+         base += gridDim.x * kWarps * kCellsPerWarp) {
+        const int nb_cells = C - base < kCellsPerWarp ? C - base : kCellsPerWarp;
         if (lane < 4 * nb_cells) {
             const int ci = lane >> 2, which = lane & 3, i = base + ci;
             const double v = which == 0 ? sa[i] : which == 1 ? ss[i] : qs[i];
             sK[wib][ci][which] = which == 3 ? inva32[i] : (float)v;
         }
-        // kTogether cells at a time share each point's table loads (directions, weights, basis)
-        for (int c0 = 0; c0 < nb_cells; c0 += kTogether) {
-            int4 nb[kTogether];
-            float nx[kTogether][3], ny[kTogether][3], g[kTogether][3];
-            const float *own[kTogether], *up[kTogether][3];
+        // a group without a cell repeats the warp's last one; its sums are not stored
+        const int i = base + (grp < nb_cells ? grp : nb_cells - 1);
+        const int4 nb = nbr[i];
+        const int nbf[3] = {nb.x, nb.y, nb.z};
+        float nx[3], ny[3], r[3];
+        const float4 *own = reinterpret_cast<const float4 *>(psi + (size_t)i * Qp);
+        const float4 *up[3];
+        const float ri = RHO ? invrho32[i] : 1.0f;
 #pragma unroll
-            for (int t = 0; t < kTogether; ++t) {
-                // a missing partner cell repeats the last real one; its sums are not stored
-                const int i = base + min(c0 + t, nb_cells - 1);
-                nb[t] = nbr[i];
+        for (int f = 0; f < 3; ++f) {
+            nx[f] = nrm32[6 * (size_t)i + 2 * f];
+            ny[f] = nrm32[6 * (size_t)i + 2 * f + 1];
+            r[f] = RHO && nbf[f] >= 0 ? invrho32[nbf[f]] : ri;
+            if (RHO && nbf[f] < 0 && bc == 0) nx[f] = ny[f] = 0.0f;  // Neumann ghost drops out
+            // upwind row: the neighbour's; on the boundary the cell's own (Neumann ghost:
+            // fluctuation 0) or the zero row (vacuum ghost: fluctuation -psi_i)
+            up[f] = nbf[f] >= 0 ? reinterpret_cast<const float4 *>(psi + (size_t)nbf[f] * Qp)
+                    : bc == 0   ? own
+                                : reinterpret_cast<const float4 *>(zrow);
+        }
+        float F[n];
 #pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    nx[t][f] = nrm32[6 * (size_t)i + 2 * f];
-                    ny[t][f] = nrm32[6 * (size_t)i + 2 * f + 1];
-                }
-                own[t] = psi + (size_t)i * Qp;
-                // upwind rows: the neighbour's row, or the cell's own row as the Neumann ghost
-                // (its fluctuation is then zero) scaled by 0 for the vacuum ghost; loads are
-                // issued unconditionally so that all rows of a point are in flight together
-                const int nbf[3] = {nb[t].x, nb[t].y, nb[t].z};
-#pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    up[t][f] = nbf[f] >= 0 ? psi + (size_t)nbf[f] * Qp : own[t];
-                    g[t][f] = (nbf[f] >= 0 || bc == 0) ? 1.0f : 0.0f;
-                }
-            }
-            float F[kTogether][n], Fc[n];
-#pragma unroll
-            for (int a = 0; a < n; ++a) Fc[a] = 0.0f;
-#pragma unroll
-            for (int t = 0; t < kTogether; ++t)
-#pragma unroll
-                for (int a = 0; a < n; ++a) F[t][a] = 0.0f;
+        for (int a = 0; a < n; ++a) F[a] = 0.0f;
 #pragma unroll 2
-            for (int q = lane; q < Qp; q += 32) {
-                const float wx = T.wox32[q], wy = T.woy32[q];
-                float Mq[n];
+        for (int j = gl; j < nq4; j += kGroup) {
+            const float4 po = __ldg(own + j);
+            const float4 p0 = __ldg(up[0] + j), p1 = __ldg(up[1] + j), p2 = __ldg(up[2] + j);
+            const float4 wx = __ldg(wx4 + j), wy = __ldg(wy4 + j);
+            const float s0 = point_fluct<RHO>(wx.x, wy.x, nx, ny, ri, r, po.x, p0.x, p1.x, p2.x);
+            const float s1 = point_fluct<RHO>(wx.y, wy.y, nx, ny, ri, r, po.y, p0.y, p1.y, p2.y);
+            const float s2 = point_fluct<RHO>(wx.z, wy.z, nx, ny, ri, r, po.z, p0.z, p1.z, p2.z);
+            const float s3 = point_fluct<RHO>(wx.w, wy.w, nx, ny, ri, r, po.w, p0.w, p1.w, p2.w);
 #pragma unroll
-                for (int a = 0; a < n; ++a) Mq[a] = T.Mt32[a * Qp + q];
-#pragma unroll
-                for (int t = 0; t < kTogether; ++t) {
-                    const float pi = __ldg(own[t] + q);
-                    float s = 0.0f;
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) {
-                        const float d = fmaf(wx, nx[t][f], wy * ny[t][f]);
-                        s = fmaf(fminf(d, 0.0f), fmaf(g[t][f], __ldg(up[t][f] + q), -pi), s);
-                    }
-#pragma unroll
-                    for (int a = 0; a < n; ++a) F[t][a] = fmaf(Mq[a], s, F[t][a]);
-                }
+            for (int a = 0; a < n; ++a) {
+                const float4 m = __ldg(M4 + (size_t)a * nq4 + j);
+                F[a] = fmaf(m.w, s3, fmaf(m.z, s2, fmaf(m.y, s1, fmaf(m.x, s0, F[a]))));
             }
-            // compensated reduce-scatter of the 32 lane sums of each cell
+        }
+        float rs[K], re[K];
+        int slot0;
+        const bool uniq = group_reduce_scatter<n>(F, gl, rs, re, slot0);
+        if (grp < nb_cells && uniq) {
 #pragma unroll
-            for (int t = 0; t < kTogether; ++t) {
-                float rs, re;
-                const int slot = warp_reduce_scatter<n>(F[t], Fc, lane, rs, re);
-                if (c0 + t < nb_cells && slot >= 0 && slot < n) sF[wib][(c0 + t) * n + slot] = rs + re;
-            }
+            for (int k = 0; k < K; ++k)
+                if (slot0 + k < n) sF[wib][grp * n + slot0 + k] = rs[k] + re[k];
         }
         __syncwarp();
         for (int idx = lane; idx < nb_cells * n; idx += 32) {
-            const int ci = idx / n, a = idx - ci * n, i = base + ci;
-            const double ua = u[(size_t)i * n + a];
-            const float* k = sK[wib][ci];
+            const int ci = idx / n, a = idx - ci * n, ic = base + ci;
+            const double ua = u[(size_t)ic * n + a];
+            const float *k = sK[wib][ci];
             // R = -sigma_a u - sigma_s (u - u_0 e_0) + q <m>: the scattering term of moment 0
             // cancels exactly
             const float sig = a == 0 ? k[0] : k[0] + k[1];
             const float R = fmaf(-sig, (float)ua, k[2] * T.mbar32[a]);
             const float inc = dt * fmaf(-k[3], sF[wib][idx], R);
-            u[(size_t)i * n + a] = ua + (double)inc;
+            u[(size_t)ic * n + a] = ua + (double)inc;
         }
         __syncwarp();
     }
@@ -253,28 +323,37 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
     int need = (C + kWarps - 1) / kWarps;
     int cap = mn->nsm * 8;
     int grid = need < cap ? (need > 0 ? need : 1) : cap;
-    // persistent grid of as many blocks as fit at once, batches of kBatch cells dealt round-robin
-    // to warps (no partial second wave)
+    // persistent grid of as many blocks as fit at once, groups of 4 cells dealt round-robin to
+    // warps (no partial second wave)
     int resident = 0;
     switch (mn->N) {
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<1>, kWarps * 32, 0); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<2>, kWarps * 32, 0); break;
-    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<3>, kWarps * 32, 0); break;
-    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<4>, kWarps * 32, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<5>, kWarps * 32, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<1, false>, kWarps * 32, 0); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<2, false>, kWarps * 32, 0); break;
+    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<3, false>, kWarps * 32, 0); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<4, false>, kWarps * 32, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, flux_update32_kernel<5, false>, kWarps * 32, 0); break;
     }
     if (resident < 1) resident = 1;
-    const int need32 = (C + kWarps * kBatch - 1) / (kWarps * kBatch);
+    const int need32 = (C + kWarps * kCellsPerWarp - 1) / (kWarps * kCellsPerWarp);
     const int grid32 = need32 < mn->nsm * resident ? (need32 > 0 ? need32 : 1) : mn->nsm * resident;
+    if (!psi && (T.Qp % 32 != 0 || !mn->d_zero32)) return KITRT_EINVAL;
+    const bool rho = mn->d_invrho != nullptr;
     LaunchScope ls(mn, PK_FLUX, s, C);
+#define FLUX_LAUNCH(NN, R)                                                                     \
+    if (psi)                                                                                   \
+        flux_update_kernel<NN, R><<<grid, kWarps * 32, 0, s>>>(                                 \
+            T, m->d_nbr, m->d_nrm, m->d_area, psi, mn->d_invrho, u, sa, ss, q, dt, bc, C);     \
+    else                                                                                       \
+        flux_update32_kernel<NN, R><<<grid32, kWarps * 32, 0, s>>>(                             \
+            T, m->d_nbr, m->d_nrm32, m->d_inva32, psi32, mn->d_zero32, mn->d_invrho32, u, sa,  \
+            ss, q, (float)dt, bc, C);
 #define FLUX_CASE(NN)                                                                          \
     case NN:                                                                                   \
-        if (psi)                                                                               \
-            flux_update_kernel<NN, double><<<grid, kWarps * 32, 0, s>>>(                        \
-                T, m->d_nbr, m->d_nrm, m->d_area, psi, u, sa, ss, q, dt, bc, C);               \
-        else                                                                                   \
-            flux_update32_kernel<NN><<<grid32, kWarps * 32, 0, s>>>(                            \
-                T, m->d_nbr, m->d_nrm32, m->d_inva32, psi32, u, sa, ss, q, (float)dt, bc, C);  \
+        if (rho) {                                                                             \
+            FLUX_LAUNCH(NN, true)                                                              \
+        } else {                                                                               \
+            FLUX_LAUNCH(NN, false)                                                             \
+        }                                                                                      \
         break;
     switch (mn->N) {
         FLUX_CASE(1)
@@ -284,6 +363,7 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
         FLUX_CASE(5)
     default: return KITRT_EINVAL;
     }
+#undef FLUX_LAUNCH
 #undef FLUX_CASE
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
@@ -294,19 +374,22 @@ int launch_flux_update(kitrt_mn *mn, const Tables &T, int C, const double *psi,
 //     dt (P_i / (2 A_i) + sigma_a,i + sigma_s,i) <= 1
 // in every cell keeps every updated ordinate a non-negative combination of non-negative values
 // (scattering and source only add), and the updated moments realizable. This is the cell-wise
-// form of dt sigma_t,max <= 1 - CFL with CFL = dt / min_i (2 A_i / P_i), which implies it.
+// form of dt sigma_t,max <= 1 - CFL with CFL = dt / min_i (2 A_i / P_i), which implies it. With a
+// density (transported value psi / rho) the outflow rate of cell i is P_i / (2 A_i rho_i).
 namespace {
 
-__global__ void stability_kernel(const double *__restrict__ hpa, const double *__restrict__ sa,
-                                 const double *__restrict__ ss, double dt, int C,
-                                 unsigned long long *__restrict__ out)
+__global__ void stability_kernel(const double *__restrict__ hpa, const double *__restrict__ invrho,
+                                 const double *__restrict__ sa, const double *__restrict__ ss,
+                                 double dt, int C, unsigned long long *__restrict__ out)
 {
     double worst = 0.0;
     unsigned bad = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
         const double a = sa[i], b = ss[i];
+        // with a density the transport speed of cell i is 1 / rho_i
+        const double h = invrho ? hpa[i] * invrho[i] : hpa[i];
         if (!(a >= 0.0) || !(b >= 0.0) || !isfinite(a) || !isfinite(b)) ++bad;
-        else worst = fmax(worst, dt * (hpa[i] + a + b));
+        else worst = fmax(worst, dt * (h + a + b));
     }
     // non-negative doubles order like their bit patterns
     unsigned long long wb = __double_as_longlong(worst);
@@ -335,8 +418,8 @@ int check_stability(kitrt_mn *mn, const double *sa, const double *ss, double dt,
     if (blocks > mn->nsm * 4) blocks = mn->nsm * 4;
     {
         LaunchScope ls(mn, PK_OTHER, s, C);
-        stability_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(mn->mesh->d_hpa, sa, ss, dt, C,
-                                                                  mn->d_check);
+        stability_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(mn->mesh->d_hpa, mn->d_invrho, sa,
+                                                                  ss, dt, C, mn->d_check);
     }
     if (cudaGetLastError() != cudaSuccess) return KITRT_ECUDA;
     if (cudaMemcpyAsync(mn->h_check, mn->d_check, 2 * sizeof(unsigned long long),

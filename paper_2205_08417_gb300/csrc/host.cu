@@ -233,6 +233,7 @@ Tables kitrt_mn::tables() const
     T.Qf = Qf;
     T.Qp = Qp;
     T.m0 = 1.0 / sqrt(4.0 * kPi);
+    T.rm0 = sqrt(4.0 * kPi);
     T.Mt = d_Mt;
     T.w = d_w;
     T.wox = d_wox;
@@ -241,6 +242,7 @@ Tables kitrt_mn::tables() const
     T.gstart = d_gstart;
     T.gidx = d_gidx;
     T.gcoef = d_gcoef;
+    T.gcoef32 = d_gcoef32;
     T.Mt32 = d_Mt32;
     T.w32 = d_w32;
     T.wox32 = d_wox32;
@@ -606,6 +608,7 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_upload(mn, &mn->d_gstart, gstart));
     TRY(dev_upload(mn, &mn->d_gidx, gidx));
     TRY(dev_upload(mn, &mn->d_gcoef, gcoef));
+    TRY(dev_upload(mn, &mn->d_gcoef32, std::vector<float>(gcoef.begin(), gcoef.end())));
     TRY(dev_upload(mn, &mn->d_Mt32, Mt32));
     TRY(dev_upload(mn, &mn->d_w32, w32));
     TRY(dev_upload(mn, &mn->d_wox32, wox32));
@@ -702,6 +705,11 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     }
     if (p.mode != KITRT_FP64) {
         TRY(dev_alloc(mn, &mn->d_psi32, C * Qp));
+        TRY(dev_alloc(mn, &mn->d_zero32, (size_t)Qp));
+        if (cudaMemset(mn->d_zero32, 0, sizeof(float) * Qp) != cudaSuccess) {
+            kitrt_mn_destroy(mn);
+            return KITRT_ECUDA;
+        }
         if (p.mode == KITRT_LEARNED) TRY(dev_alloc(mn, &mn->d_alpha_nn, C * (size_t)n));
         TRY(dev_alloc(mn, &S.h64, C));
         TRY(dev_alloc(mn, &S.gnorm, C));

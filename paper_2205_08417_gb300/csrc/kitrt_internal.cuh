@@ -45,6 +45,7 @@ struct kitrt_mesh {
 struct Tables {
     int n, n2, Qf, Qp;        // moments, degree-2N moments, folded points, padded points
     double m0;                // m_0 = 1/sqrt(4 pi)
+    double rm0;               // 1 / m_0 = sqrt(4 pi)
     const double *Mt;         // [n2 x Qp] extended basis at folded points (first n rows = basis)
     const double *w;          // [Qp] folded weights (0 on padding)
     const double *wox, *woy;  // [Qp] w * Omega_x, w * Omega_y
@@ -52,6 +53,7 @@ struct Tables {
     const int32_t *gstart;    // [npairs + 1] Gaunt term ranges per packed pair (a >= b)
     const int32_t *gidx;      // [nnz] extended-moment index c
     const double *gcoef;      // [nnz] <m_a m_b m~_c>
+    const float *gcoef32;     // [nnz] FP32 copy (the mixed modes' FP32 Hessian)
     const float *Mt32;        // [n2 x Qp] FP32 copy
     const float *w32;
     const float *wox32, *woy32;  // FP32 copies of w * Omega
@@ -119,6 +121,7 @@ struct kitrt_mn {
     // device tables
     double *d_Mt = nullptr, *d_w = nullptr, *d_wox = nullptr, *d_woy = nullptr;
     double *d_mbar = nullptr, *d_gcoef = nullptr;
+    float *d_gcoef32 = nullptr;
     int32_t *d_gstart = nullptr, *d_gidx = nullptr;
     float *d_Mt32 = nullptr, *d_w32 = nullptr;
     float *d_Mhi32 = nullptr;            // [NP x Qp] TF32-rounded degree-(N+1..2N) basis (mixed)
@@ -144,6 +147,12 @@ struct kitrt_mn {
     void *d_psif = nullptr;    // second order: [C x 3 x Qp] reconstructed face values (FP64/FP32)
     double *d_ustage = nullptr;  // second order: [C x n] the Heun stage u*
     float *d_psi32 = nullptr;  // [C x Qp] FP32 ansatz (mixed modes)
+    float *d_zero32 = nullptr; // [Qp] zeros: the vacuum ghost's row in the FP32 flux
+    // transformed CSD equation (kitrt_mn_set_density): 1 / rho per cell, FP64 and FP32 (NULL:
+    // no density, rho = 1)
+    double *d_invrho = nullptr;
+    float *d_invrho32 = nullptr;
+    double *d_rho_store = nullptr;  // [2 C] owned storage behind d_invrho / d_invrho32
     int32_t *h_cnt = nullptr;  // pinned copy of st.cnt
     // kitrt_mn_reset: the next kitrt_step starts every cell from its given alpha (otherwise each
     // cell whose given alpha is the one the solver last returned continues from its stored state)

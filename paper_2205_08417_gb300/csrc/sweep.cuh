@@ -117,6 +117,42 @@ __device__ __forceinline__ float exp_to_float(double e)
     return f >= (255LL << 23) ? __int_as_float(0x7f800000) : __int_as_float((int)f);
 }
 
+// Conversions done in integer arithmetic, so that the narrow FP64 pipe does not execute them.
+// Whether a double is finite (exponent field not all ones).
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
+// A finite double rounded to float: the exponent rebiased and the mantissa rounded half away from
+// zero at bit 29 (a carry into the exponent is the correct result); magnitudes below the smallest
+// normal float give a signed zero, magnitudes beyond the float range a signed infinity.
+__device__ __forceinline__ float d2f_bits(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const long long mag = b & 0x7fffffffffffffffLL;
+    const int sign = (int)((unsigned long long)b >> 32) & (int)0x80000000u;
+    if ((int)(mag >> 52) < 1023 - 126) return __int_as_float(sign);
+    long long f = ((mag + (1LL << 28)) >> 29) - ((long long)(1023 - 127) << 23);
+    if (f >= (255LL << 23)) f = 255LL << 23;
+    return __int_as_float((int)f | sign);
+}
+
+// A float widened to double exactly; subnormal floats give a signed zero, infinities and NaNs
+// stay infinities and NaNs.
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned mag = b & 0x7fffffffu;
+    if (mag < 0x00800000u) return __longlong_as_double((long long)sign);
+    if (mag >= 0x7f800000u)
+        return __longlong_as_double((long long)(sign | 0x7ff0000000000000ULL |
+                                                ((unsigned long long)(mag & 0x7fffffu) << 29)));
+    return __longlong_as_double(
+        (long long)(sign | (((unsigned long long)mag << 29) + ((unsigned long long)(1023 - 127) << 52))));
+}
+
 // Split of a sweep's work: tiles of 128 listed cells times parts of the quadrature (units of 16
 // pairs). When few cells are listed each tile's quadrature is split over up to `nunits` parts so
 // that every SM gets work; part j of list slot i lands in column j * cnt + i of the accumulator,
