@@ -67,6 +67,11 @@ def _declare(L):
     L.orc_ansatz.argtypes = [i, i, i, _dp, _dp, _dp, i]
     L.orc_flux_update.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
                                   d, i, _dp, i]
+    L.orc_flux_update_rho.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp,
+                                      _dp, _dp, d, i, _dp, i]
+    L.orc_mn_run_rho.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, _dp,
+                                 d, i, i, d, i, i, i, _dp, _dp, _ip]
+    L.orc_dose_accumulate.argtypes = [i, i, d, _dp, _dp, d, d, _dp]
     L.orc_mn_run.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp, d, i, i,
                              d, i, i, i, _dp, _dp, _ip]
     L.orc_mn_adjoint.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _ip, i, _dp, _dp,
@@ -231,6 +236,35 @@ def flux_update(T: Tables, G: Geometry, psi, u, sigma_a, sigma_s, qsrc, dt, bc=0
                           _d(np.ascontiguousarray(sigma_s, dtype=np.float64)),
                           _d(np.ascontiguousarray(qsrc, dtype=np.float64)), dt, bc, _d(u),
                           nthreads)
+
+
+def flux_update_rho(T: Tables, G: Geometry, rho, psi, u, sigma_a, sigma_s, qsrc, dt, bc=0,
+                    nthreads=0):
+    """In-place flux + source + update of the transformed CSD equation (psi / rho transported)."""
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    lib().orc_flux_update_rho(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                              _d(G.nrm), _d(G.area), f(rho), _d(np.ascontiguousarray(psi)),
+                              f(sigma_a), f(sigma_s), f(qsrc), dt, bc, _d(u), nthreads)
+
+
+def mn_run_rho(T: Tables, G: Geometry, rho, u, alpha, sigma_a, sigma_s, qsrc, dt, nsteps, bc=0,
+               tau=1e-10, max_iter=100, polish=True, nthreads=0):
+    """nsteps first-order M_N steps of the transformed CSD equation with density rho per cell,
+    in place. Returns (n_failed, status)."""
+    st = np.zeros(G.C, dtype=np.int32)
+    f = lambda a: _d(np.ascontiguousarray(a, dtype=np.float64))
+    nf = lib().orc_mn_run_rho(G.C, T.n, T.Q, _d(T.M), _d(T.w), _d(T.ox), _d(T.oy), _i(G.nbr),
+                              _d(G.nrm), _d(G.area), f(rho), f(sigma_a), f(sigma_s), f(qsrc), dt,
+                              bc, nsteps, tau, max_iter, int(polish), nthreads, _d(u), _d(alpha),
+                              _i(st))
+    return nf, st
+
+
+def dose_accumulate(T: Tables, u, rho, S, dt, dose):
+    """dose += dt S u_0 / (m_0 rho), in place (one pseudo-time step of the dose integral)."""
+    lib().orc_dose_accumulate(u.shape[0], T.n, T.m0, _d(np.ascontiguousarray(u)),
+                              _d(np.ascontiguousarray(rho, dtype=np.float64)), float(S), float(dt),
+                              _d(dose))
 
 
 def reconstruct(G: Geometry, psi, bc=0):

@@ -545,6 +545,92 @@ void orc_flux_update(int C, int n, int Q, const double *M, const double *w, cons
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Heterogeneous density of the CSD equation in pseudo-time [Sec. 2, Eq. BoltzmannCSDTrafo]      */
+/* ------------------------------------------------------------------------------------------ */
+
+/* The transformed CSD equation transports psi / rho(x): its flux term is Omega . grad(psi / rho),
+ * with rho the tissue density per cell, and its cross sections depend on the pseudo-time only.
+ * So the kinetic flux of the step is orc_flux_update's with the upwind value psi_up / rho_up
+ * (the cell's own psi_i / rho_i on an outflow face; across a face the neighbour's psi_j / rho_j;
+ * on a boundary face psi_i / rho_i (Neumann) or 0 (vacuum)); the update and source are
+ * unchanged (sigma_a, sigma_s per cell carry Sigma_t - Sigma_s and Sigma_s at this pseudo-time). */
+void orc_flux_update_rho(int C, int n, int Q, const double *M, const double *w, const double *ox,
+                         const double *oy, const int32_t *nbr, const double *nrm,
+                         const double *area, const double *rho, const double *psi,
+                         const double *sigma_a, const double *sigma_s, const double *qsrc,
+                         double dt, int bc, double *u, int nthreads)
+{
+    double mbar[64];
+    for (int a = 0; a < n; ++a) {
+        mbar[a] = 0.0;
+        for (int q = 0; q < Q; ++q) mbar[a] += w[q] * M[(size_t)q * n + a];
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(static)
+#endif
+    for (int i = 0; i < C; ++i) {
+        double F[64];
+        for (int a = 0; a < n; ++a) F[a] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            int j = nbr[3 * i + k];
+            double nx = nrm[6 * i + 2 * k], ny = nrm[6 * i + 2 * k + 1];
+            for (int q = 0; q < Q; ++q) {
+                double dot = ox[q] * nx + oy[q] * ny;
+                double up;
+                if (dot > 0.0)
+                    up = psi[(size_t)i * Q + q] / rho[i];
+                else if (j >= 0)
+                    up = psi[(size_t)j * Q + q] / rho[j];
+                else
+                    up = (bc == 0) ? psi[(size_t)i * Q + q] / rho[i] : 0.0;
+                double s = w[q] * dot * up;
+                for (int a = 0; a < n; ++a) F[a] += s * M[(size_t)q * n + a];
+            }
+        }
+        double *ui = u + (size_t)i * n;
+        double u0 = ui[0];
+        for (int a = 0; a < n; ++a) {
+            double R = -sigma_a[i] * ui[a] - sigma_s[i] * (ui[a] - (a == 0 ? u0 : 0.0)) +
+                       qsrc[i] * mbar[a];
+            ui[a] = ui[a] - dt / area[i] * F[a] + dt * R;
+        }
+    }
+    (void)nthreads;
+}
+
+/* nsteps first-order M_N steps of the transformed CSD equation with density rho per cell. */
+int orc_mn_run_rho(int C, int n, int Q, const double *M, const double *w, const double *ox,
+                   const double *oy, const int32_t *nbr, const double *nrm, const double *area,
+                   const double *rho, const double *sigma_a, const double *sigma_s,
+                   const double *qsrc, double dt, int bc, int nsteps, double tau, int max_iter,
+                   int polish, int nthreads, double *u, double *alpha, int32_t *status)
+{
+    double *psi = (double *)malloc(sizeof(double) * (size_t)C * Q);
+    int nfail = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        nfail += orc_closure_batch_reg(C, n, Q, M, w, u, alpha, tau, max_iter, 30, 1e-4, polish,
+                                       0.0, 1, nthreads, status, NULL);
+        orc_ansatz(C, n, Q, M, alpha, psi, nthreads);
+        orc_flux_update_rho(C, n, Q, M, w, ox, oy, nbr, nrm, area, rho, psi, sigma_a, sigma_s,
+                            qsrc, dt, bc, u, nthreads);
+    }
+    free(psi);
+    return nfail;
+}
+
+/* Dose [Sec. 2]: D(x) = 1/rho int_E int_S2 S(E, x) psi dOmega dE with S(E, x) = S_w(E) rho(x)
+ * (water-equivalent tissue). In the transformed variables psi~ = S_w rho psi and
+ * dE = S_w(E(E~)) dE~, so D = 1/rho int Phi~(E~) S_w(E(E~)) dE~ with Phi~ = int psi~ dOmega =
+ * u_0 / m_0. One explicit pseudo-time step of length dt at stopping power S adds
+ * dt S u_i0 / (m_0 rho_i) to cell i (left endpoint rule). */
+void orc_dose_accumulate(int C, int n, double m0, const double *u, const double *rho, double S,
+                         double dt, double *dose)
+{
+    for (int i = 0; i < C; ++i) dose[i] += dt * S * (u[(size_t)i * n] / m0) / rho[i];
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Second-order scheme [Sec. 4.3]: linear reconstruction with the Green-Gauss gradient and the   */
 /* Barth-Jespersen limiter, second-order upwind (kinetic) flux, Heun time stepping              */
 /* ------------------------------------------------------------------------------------------ */
