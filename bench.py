@@ -226,17 +226,23 @@ def log(msg):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
-def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None, **opts):
+def run_mode(K, torch, W, mode, steps, warmup, t_start, tau, e2e=True, net=None, density=None,
+             cfl=0.4, **opts):
     mesh = K.Mesh(W["mesh"].xy, W["mesh"].tri)
     s = K.MNSolver(mesh, W["N"], W["order"], mode=mode, tau=tau, **opts)
     if net is not None:
         s.set_mlp(net.params, net.norm)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    u = d(W["u0"])
+    u0 = W["u0"] if density is None else W["u0"] * density[:, None]
+    u = d(u0)
     alpha = s.isotropic_alpha(u)
     sa, ss, q = d(W["sa"]), d(W["ss"]), d(W["q"])
     geo = mesh.geometry()
-    dt = 0.4 * geo["min_inradius"]
+    dt = cfl * geo["min_inradius"]
+    if density is not None:
+        # the transformed CSD equation transports psi / rho: speed 1 / rho
+        s.set_density(d(density))
+        dt *= float(density.min())
     setup = int(round(t_start / dt))
     before = 0
     t0 = time.perf_counter()
@@ -407,9 +413,41 @@ def run_extras(K, torch, args, peak, hbm_peak, head_results):
     ex["d2_regularized_mixed_tf32"] = dict(mode_line(W, r, steps), reg_gamma=1e-3, reg_keep_mass=1)
     log(f"extra regularized: {r['ms'] / steps:.3f} ms/step")
 
+    # the transformed CSD equation (psi / rho transported) on the same mesh with a two-tissue
+    # density (1 | 5, and a disc of 2.5): the line-source start scaled by rho, pseudo-time steps
+    from paper_2205_08417_gb300 import synth
+    rho = synth.two_tissue_density(W["cen"])
+    csd = {}
+    for mode, tau in (("mixed_tf32", args.tau_mixed), ("fp64", args.tau)):
+        r = run_mode(K, torch, W, mode, steps, args.warmup, args.t_start, tau, e2e=False,
+                     density=rho)
+        csd[mode] = r
+        ex[f"d2_csd_density_{mode}"] = dict(mode_line(W, r, steps), density="two_tissue 1|5, disc 2.5")
+        log(f"extra CSD density {mode}: {r['ms'] / steps:.3f} ms/step")
+    ex["d2_csd_density_mixed_tf32"]["u0_rel_l2_vs_fp64"] = float(
+        np.linalg.norm(csd["mixed_tf32"]["u"][:, 0] - csd["fp64"]["u"][:, 0]) /
+        np.linalg.norm(csd["fp64"]["u"][:, 0]))
+
+    # the checkerboard of Sec. 7.2 as the paper runs it: M_3, second-order flux with Heun, CFL
+    # 0.45, vacuum walls, 25,088 triangles, from the 1e-4 floor to pseudo-time 1
+    Wc = make_workload("m3_checkerboard_25k")
+    Wc["sa"], Wc["ss"], Wc["q"] = synth.checkerboard_medium(Wc["cen"])
+    Wc["u0"] = np.zeros((Wc["C"], Wc["n"]))
+    Wc["u0"][:, 0] = 1e-4 / math.sqrt(4 * math.pi)
+    cb = {}
+    for mode, tau in (("mixed_tf32", args.tau_mixed), ("fp64", args.tau)):
+        r = run_mode(K, torch, Wc, mode, steps, args.warmup, 1.0, tau, e2e=False, cfl=0.45,
+                     order=2, bc="vacuum")
+        cb[mode] = r
+        ex[f"checkerboard_m3_second_order_{mode}"] = dict(mode_line(Wc, r, steps), cells=Wc["C"],
+                                                          cfl=0.45, t_start=1.0)
+        log(f"extra checkerboard {mode}: {r['ms'] / steps:.3f} ms/step")
+    ex["checkerboard_m3_second_order_mixed_tf32"]["u0_rel_l2_vs_fp64"] = float(
+        np.linalg.norm(cb["mixed_tf32"]["u"][:, 0] - cb["fp64"]["u"][:, 0]) /
+        np.linalg.norm(cb["fp64"]["u"][:, 0]))
+
     # adjoint configuration: 7x7 block medium on [0,7]^2, M_3, order 10, 400 steps, checkpoints
     # every 16, absorbed energy of the centre 3x3 blocks and its 98 gradients
-    from paper_2205_08417_gb300 import synth
     spec = synth.WORKLOADS["m3_blocks_60k"]
     m = synth.jittered_mesh(spec["k"], spec["lo"], spec["hi"], spec["seed"])
     cen = m.centroids()

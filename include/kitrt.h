@@ -269,6 +269,35 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
                    const double *sigma_s, const double *q, double dt, int32_t nsteps,
                    int32_t *status, void *stream, kitrt_stats *stats);
 
+/* Heterogeneous density of the transformed CSD equation [Sec. 2, Eq. BoltzmannCSDTrafo]. After
+ * the energy transform the CSD equation is a transport equation in the pseudo-time t (the
+ * transformed energy) whose flux term is Omega . grad(psi / rho), rho(x) the tissue density, and
+ * whose cross sections depend on t only. With a density set, every later first-order kitrt_step
+ * of this solver transports psi / rho: the kinetic upwind flux takes psi_up / rho_up across each
+ * face (psi_i / rho_i on outflow faces and for the Neumann ghost, 0 for the vacuum ghost); the
+ * closure, the source term and the arrays sigma_a, sigma_s, q keep their meaning (for the CSD
+ * equation the caller passes this pseudo-time step's Sigma_t - Sigma_s and Sigma_s in every cell).
+ * The stability condition of kitrt_step becomes dt (P_i / (2 A_i rho_i) + sigma_a,i + sigma_s,i)
+ * <= 1, and dt <= 0 still selects cfl * min_i 2 A_i / P_i, which the test then rejects where
+ * rho < 1: pass dt explicitly.
+ *   rho   device [C] FP64, every entry positive and finite; the solver keeps 1/rho (FP64 and FP32
+ *         copies in its workspace, allocated on the first call). NULL removes the density.
+ * KITRT_EINVAL when an entry is not positive and finite (the solver is then left without a
+ * density). Synchronises with `stream`. While a density is set, kitrt_step with order 2,
+ * kitrt_adjoint and kitrt_sn_step return KITRT_EINVAL. */
+int32_t kitrt_mn_set_density(kitrt_mn *mn, const double *rho, void *stream);
+
+/* Dose [Sec. 2: D(x) = 1/rho int int S(E, x) psi dOmega dE with S(E, x) = S_w(E) rho(x)] of one
+ * explicit pseudo-time step. In the transformed variables psi~ = S_w rho psi and dE = S_w dE~,
+ * so D = 1/rho int Phi~ S_w dE~ with Phi~ = int psi~ dOmega = u_0 / m_0; the step adds
+ *   dose_i += dt * S * u_i0 / (m_0 rho_i)
+ * (rho = 1 without a density), S the water stopping power S_w at this step's energy (the
+ * caller's table: the ICRU data the paper uses are not part of the library).
+ *   u     device [C x n] the state at the start of the step; dose device [C] FP64, accumulated.
+ * Asynchronous on `stream`. KITRT_EINVAL for NULL pointers or non-finite S or dt. */
+int32_t kitrt_dose_accumulate(kitrt_mn *mn, const double *u, double S, double dt, double *dose,
+                              void *stream);
+
 /* Entropy closure of a batch of moment vectors without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot let the library allocate device
  * memory at call time, for instance a framework whose pool allocator already owns the free device

@@ -191,7 +191,7 @@ extern "C" int32_t kitrt_adjoint(kitrt_mn *mn, const double *u0, const double *a
 {
     if (!mn || !u0 || !alpha0 || !sigma_a || !sigma_s || !q || !block_of_cell || !target || !J ||
         !dJ_dsa || !dJ_dss || nblocks < 1 || nsteps < 0 || ckpt_every < 1 || mn->p.mode != KITRT_FP64 ||
-        mn->p.order != 1 || mn->p.reg_gamma != 0.0)
+        mn->p.order != 1 || mn->p.reg_gamma != 0.0 || mn->d_invrho)
         return KITRT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int C = mn->mesh->C, n = mn->n, Qp = mn->Qp;

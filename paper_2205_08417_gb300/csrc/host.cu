@@ -950,6 +950,8 @@ int32_t kitrt_step(kitrt_mn *mn, double *u, double *alpha, const double *sigma_a
                    int32_t *status, void *stream, kitrt_stats *stats)
 {
     if (!mn || !u || !alpha || !sigma_a || !sigma_s || !q || nsteps < 0) return KITRT_EINVAL;
+    // the density of the transformed CSD equation is applied by the first-order flux only
+    if (mn->d_invrho && mn->p.order != 1) return KITRT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (dt <= 0.0) dt = mn->p.cfl * mn->mesh->min_inradius;
     if (stats) {

@@ -433,7 +433,8 @@ int32_t kitrt_sn_step(kitrt_mn *mn, void *psi, void *work, int32_t fp32, const d
                       const double *sigma_s, const double *q, const double *g, double dt,
                       int32_t nsteps, void *stream)
 {
-    if (!mn || !psi || !work || !sigma_a || !sigma_s || !q || nsteps < 0) return KITRT_EINVAL;
+    if (!mn || !psi || !work || !sigma_a || !sigma_s || !q || nsteps < 0 || mn->d_invrho)
+        return KITRT_EINVAL;
     // rows are staged with 16-byte bulk copies
     if (((uintptr_t)psi | (uintptr_t)work) & 15) return KITRT_EINVAL;
     const size_t bytes = (fp32 ? 4 : 8) * (size_t)mn->mesh->C * mn->Qf;

@@ -81,6 +81,8 @@ SIGNATURES = {
     "kitrt_ansatz": (C.c_int32, [_vp, _vp, _vp, _vp]),
     "kitrt_step": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int32, _vp, _vp,
                                C.POINTER(Stats)]),
+    "kitrt_mn_set_density": (C.c_int32, [_vp, _vp, _vp]),
+    "kitrt_dose_accumulate": (C.c_int32, [_vp, _vp, C.c_double, C.c_double, _vp, _vp]),
     "kitrt_adjoint": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, _vp, C.c_double,
                                   C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
     "kitrt_mlp_param_count": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32]),
@@ -345,6 +347,20 @@ class MNSolver:
         if check:
             _check(rc, "kitrt_step")
         return (rc, st.as_dict()) if stats else rc
+
+    def set_density(self, rho):
+        """Density per cell of the transformed CSD equation (FP64 CUDA tensor [C]), or None to
+        remove it: later first-order steps transport psi / rho."""
+        import torch
+        _check(_lib().kitrt_mn_set_density(self.handle, _dev(rho, torch.float64), _stream()),
+               "kitrt_mn_set_density")
+
+    def dose_accumulate(self, u, S: float, dt: float, dose):
+        """dose += dt S u_0 / (m_0 rho): one pseudo-time step of the dose (FP64 CUDA tensors)."""
+        import torch
+        _check(_lib().kitrt_dose_accumulate(self.handle, _dev(u, torch.float64), float(S),
+                                            float(dt), _dev(dose, torch.float64), _stream()),
+               "kitrt_dose_accumulate")
 
     def reset(self):
         """Forget the closure state kept for continuation: the next step starts from its alpha."""

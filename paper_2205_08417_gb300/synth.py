@@ -111,6 +111,41 @@ def block_coefficients(cen: np.ndarray, lo: float, hi: float, nb: int, seed: int
     return blk, sa, ss
 
 
+# Checkerboard (Sec. 7.2): on [0,7]^2 of 7 x 7 unit blocks, a source block X_q in the centre and
+# absorbing blocks X_a in a checkerboard pattern around it. The paper's layout figure is lost; the
+# absorbers here are the blocks (i, j), 1 <= i, j <= 5, with i + j even, except the source block
+# (3, 3) and the block (3, 5) above it, so that, as the paper describes, radiation leaves the
+# source freely upwards and is damped to the left, the right and below.
+CHECKERBOARD_ABSORBERS = tuple((i, j) for i in range(1, 6) for j in range(1, 6)
+                               if (i + j) % 2 == 0 and (i, j) not in ((3, 3), (3, 5)))
+
+
+def checkerboard_medium(cen: np.ndarray):
+    """Cross sections and source of the checkerboard (Sec. 7.2) at cell centroids on [0,7]^2:
+    absorbers sigma_t = 10, sigma_s = 0 (sigma_a = 10); elsewhere sigma_t = sigma_s = 1
+    (sigma_a = 0); isotropic source q = 1 in the centre block. Cells are assigned to blocks by
+    centroid. Returns (sigma_a, sigma_s, q)."""
+    b = np.clip(np.floor(cen).astype(np.int64), 0, 6)
+    absorb = np.zeros(cen.shape[0], dtype=bool)
+    for i, j in CHECKERBOARD_ABSORBERS:
+        absorb |= (b[:, 0] == i) & (b[:, 1] == j)
+    sa = np.where(absorb, 10.0, 0.0)
+    ss = np.where(absorb, 0.0, 1.0)
+    q = np.where((b[:, 0] == 3) & (b[:, 1] == 3), 1.0, 0.0)
+    return sa, ss, q
+
+
+def two_tissue_density(cen: np.ndarray, split: float = 0.0, hi: float = 5.0,
+                       disc=(-0.4, 0.3, 0.25, 2.5)):
+    """A heterogeneous density for the transformed CSD equation (Sec. 2): 1 left of x = split,
+    `hi` right of it (the density jump 1 -> 5 of the paper's Sec. 7.1 comparison), and a disc
+    (x, y, radius, value)."""
+    rho = np.where(cen[:, 0] > split, hi, 1.0)
+    x, y, r, v = disc
+    rho[np.hypot(cen[:, 0] - x, cen[:, 1] - y) < r] = v
+    return rho
+
+
 def vmf_mixtures(count: int, seed: int, max_lobes: int = 4, kappa_lo: float = 0.1,
                  kappa_hi: float = 50.0):
     """Random angular densities: mixtures of 1..max_lobes von Mises-Fisher lobes on S^2.
@@ -145,4 +180,6 @@ WORKLOADS = {
     "m3_line_source_100k": dict(k=224, lo=-1.5, hi=1.5, seed=2, N=3, order=20),
     "m3_blocks_60k": dict(k=173, lo=0.0, hi=7.0, seed=3, N=3, order=10),
     "m5_line_source_1m": dict(k=707, lo=-1.5, hi=1.5, seed=5, N=5, order=30, blocks=True),
+    # the checkerboard of Sec. 7.2 (25,000 cells in the paper; 2 x 112^2 = 25,088 here)
+    "m3_checkerboard_25k": dict(k=113, lo=0.0, hi=7.0, seed=6, N=3, order=10),
 }
