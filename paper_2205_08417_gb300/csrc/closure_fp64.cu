@@ -551,6 +551,46 @@ int launch_isotropic(const Tables &T, int C, const double *u, double *alpha, cud
     return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
 }
 
+// Sum of each listed slot's quadrature parts (written by the sweeps, sweep.cuh) into its part-0
+// column, in order, element-wise over the [n2 x cnt] moments with every SM taking part, so that
+// the Newton kernel's serial per-cell chain reads one column instead of `parts`. Tensor-core
+// rows' Hessian-only moments (degree > N) are FP32 accumulator values and are added in FP32; the
+// gradient moments, and every moment of a row handed to the FP64 sweep (its part 0 holds the
+// FP64 sums, its other parts zeros), in FP64.
+__global__ void sum_parts_kernel(NewtonState S, int k, double *__restrict__ Vacc, int vs, int n,
+                                 int n2, int target_items, int nunits, int mixed)
+{
+    const int cnt = S.cnt[k % 3];
+    const int parts = sweep_split(cnt, target_items, nunits).parts;
+    if (parts <= 1) return;
+    const int32_t *list = S.list[k & 1];
+    const size_t total = (size_t)n2 * cnt, pstride = (size_t)cnt;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / cnt), j = (int)(e - (size_t)c * cnt);
+        double *col = Vacc + (size_t)c * vs + j;
+        if (mixed && c >= n && !S.h64[list[j]]) {
+            float v = d2f_bits(col[0]);
+            for (int p = 1; p < parts; ++p) v += d2f_bits(col[(size_t)p * pstride]);
+            col[0] = f2d_bits(v);
+        } else {
+            double v = col[0];
+            for (int p = 1; p < parts; ++p) v += col[(size_t)p * pstride];
+            col[0] = v;
+        }
+    }
+}
+
+int launch_sum_parts(kitrt_mn *mn, const NewtonState &S, int k, double *Vacc, cudaStream_t s)
+{
+    const int mixed = mn->p.mode != KITRT_FP64;
+    LaunchScope ls(mn, PK_POST, s, 0);
+    sum_parts_kernel<<<mn->nsm * 8, 256, 0, s>>>(S, k, Vacc, mn->vs, mn->n, mn->n2,
+                                                 mixed ? mn->target_mixed : mn->target_fp64,
+                                                 mn->Qp / 32, mixed);
+    return cudaGetLastError() == cudaSuccess ? KITRT_OK : KITRT_ECUDA;
+}
+
 int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u, int k,
                 NewtonParams np, double *Vacc, cudaStream_t s)
 {
@@ -559,7 +599,8 @@ int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, cons
     int blocks = (C + kPostBlock - 1) / kPostBlock;
     if (blocks > mn->nsm * 32) blocks = mn->nsm * 32;
     const int mixed = mn->p.mode != KITRT_FP64;
-    const int target = mixed ? mn->target_mixed : mn->target_fp64;
+    // sum_parts_kernel has added the sweeps' parts into part 0 (target 0 gives one part)
+    const int target = 0;
     const size_t smem = post_smem_bytes(mn->n, mn->n2, mn->npairs, mn->gaunt_nnz, mixed != 0,
                                         kUnrolledNewton && mn->N <= 3);
     int rc = KITRT_OK;

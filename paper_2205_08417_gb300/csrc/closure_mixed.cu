@@ -27,51 +27,19 @@
 #include "kitrt_internal.cuh"
 #include "kexp.cuh"
 #include "newton_common.cuh"
+#include "async_copy.cuh"
 #include "sweep.cuh"
 
 namespace {
 
 using namespace kitrt_dev;
+using namespace kitrt_async;
 
 constexpr int kTileM = 128;   // cells per tile (MMA M)
 constexpr int kChunk = 32;    // quadrature points per chunk (MMA K per chunk)
 constexpr int kThreads = 256;
 constexpr int kWarpsM = kThreads / 32;
-constexpr long kWaitLimit = 1L << 20;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// ----- tcgen05 / mbarrier wrappers -----------------------------------------------------------
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    for (long i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
+// ----- tcgen05 wrappers (mbarrier helpers: async_copy.cuh) -------------------------------------
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -843,10 +843,12 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
         if (!rc) rc = launch_learned_pass(mn, T, mn->st, C, u, psi32, first == 1, s);
         if (rc) return rc;
     }
-    const int batch = 4;
+    // rounds are launched in batches between two reads of the counters; the first batch is as long
+    // as the previous closure needed (its largest evaluation count), so that a steady run launches
+    // no empty round and synchronises once
     const int max_launch = (mn->p.max_iter + 1) * (mn->p.max_halvings + 1) + 1;
     int k = 0;
-    for (;;) {
+    for (int batch = mn->pass_hint;; batch = 4) {
         for (int b = 0; b < batch; ++b, ++k) {
             // quadrature sweeps write each listed cell's moment row; the thread-per-cell Newton
             // step then takes every listed cell
@@ -859,6 +861,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
                 rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, true, psi32, mn->d_Vacc);
                 if (!rc) rc = launch_eval_mixed(mn, T, mn->st, C, u, k, np, s, psi32);
             }
+            if (!rc) rc = launch_sum_parts(mn, mn->st, k, mn->d_Vacc, s);
             if (!rc) rc = launch_post(mn, T, mn->st, C, u, k, np, mn->d_Vacc, s);
             if (rc) return rc;
         }
@@ -869,6 +872,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
         if (active == 0) break;
         if (k >= max_launch) return KITRT_ETIMEOUT;
     }
+    mn->pass_hint = std::max(1, std::min(8, (int)mn->h_cnt[4]));
     // the sweeps' evaluations (the network's residual passes run in their own kernel)
     if (mn->prof_on) mn->prof_units[mn->p.mode == KITRT_FP64 ? PK_EVAL : PK_EVAL_MIXED] += mn->h_cnt[6];
     if (mn->prof_on && mn->p.mode == KITRT_LEARNED) mn->prof_units[PK_MLP] += mn->h_cnt[10];

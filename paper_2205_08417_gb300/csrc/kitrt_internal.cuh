@@ -157,6 +157,7 @@ struct kitrt_mn {
     // kitrt_mn_reset: the next kitrt_step starts every cell from its given alpha (otherwise each
     // cell whose given alpha is the one the solver last returned continues from its stored state)
     bool force_cold = false;
+    int pass_hint = 4;  // rounds in the first batch of a closure (the last closure's evaluations)
     // stability test of kitrt_step / kitrt_adjoint: [0] largest dt (P/2A + sigma_a + sigma_s) as
     // the bits of a non-negative double, [1] cells with a negative or non-finite coefficient
     unsigned long long *d_check = nullptr, *h_check = nullptr;
@@ -243,6 +244,7 @@ int mixed_sweep_grid(const kitrt_mn *mn);
 int launch_eval_fp64(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,
                      const double *u, int k, NewtonParams np, cudaStream_t s,
                      bool filter = false, float *psi32 = nullptr, double *Vacc = nullptr);
+int launch_sum_parts(kitrt_mn *mn, const NewtonState &S, int k, double *Vacc, cudaStream_t s);
 int launch_post(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C, const double *u, int k,
                 NewtonParams np, double *Vacc, cudaStream_t s);
 int launch_finish(kitrt_mn *mn, const Tables &T, const NewtonState &S, int C,

@@ -24,14 +24,16 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "async_copy.cuh"
 #include "kitrt_internal.cuh"
 
 namespace {
 
+using namespace kitrt_async;
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr long kWaitLimit = 1L << 20;
 constexpr int kTileBytes = 16384;  // target size of one staged tile
 constexpr int kHeader = 128;       // shared-memory header: two mbarriers and the abort flag
 
@@ -69,55 +71,6 @@ __global__ void sn_cell_prep_kernel(const double *__restrict__ nrm, const double
         c[10] = P(0);
         c[11] = P(0);
     }
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    for (long i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to shared
-// memory, completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
 }
 
 template <typename P>
@@ -185,7 +138,7 @@ __device__ __forceinline__ void issue_tile(const P *psi, int t, int TC, int C, i
     const uint32_t nb = bulk_part((size_t)rows * Qf * sizeof(P));
     // the buffer was last read through the generic proxy: order those reads before the async
     // proxy writes it again
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_proxy_async_smem();
     mbar_expect_tx(bar, nb);
     if (nb > 0) bulk_g2s(buf, psi + (size_t)t * TC * Qf, nb, bar);
 }
