@@ -855,10 +855,11 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
             if (mn->p.mode == KITRT_FP64) {
                 rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, false, nullptr, mn->d_Vacc);
             } else {
-                // FP64 sweep of the cells handed over in earlier rounds, then the tensor-core sweep
-                // of the others (cells handed over now wait for the next round, so no cell is
-                // evaluated twice in one round)
-                rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, true, psi32, mn->d_Vacc);
+                // FP64 sweep of the cells handed over in earlier rounds (none in the first: the
+                // closure starts with every hand-over cleared), then the tensor-core sweep of the
+                // others (cells handed over now wait for the next round, so no cell is evaluated
+                // twice in one round)
+                if (k > 0) rc = launch_eval_fp64(mn, T, mn->st, C, u, k, np, s, true, psi32, mn->d_Vacc);
                 if (!rc) rc = launch_eval_mixed(mn, T, mn->st, C, u, k, np, s, psi32);
             }
             if (!rc) rc = launch_sum_parts(mn, mn->st, k, mn->d_Vacc, s);

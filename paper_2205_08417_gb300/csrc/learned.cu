@@ -48,7 +48,7 @@ learned_pass_kernel(Tables T, NewtonState S, const double *__restrict__ u,
 #pragma unroll
             for (int a = 1; a < n; ++a) z = fma(atv[a], T.Mt[a * Qp + q], z);
             const double ez = kexp(z, T.exptab);
-            if (psi32) psi32[(size_t)cell * Qp + q] = (float)ez;
+            if (psi32) psi32[(size_t)cell * Qp + q] = exp_to_float(ez);
             const double e = T.w[q] * ez;
 #pragma unroll
             for (int a = 0; a < n; ++a) Up[a] = fma(e, T.Mt[a * Qp + q], Up[a]);

@@ -307,12 +307,14 @@ mlp_infer_kernel(const __nv_bfloat16 *__restrict__ wq, const float *__restrict__
     constexpr int nthr = 128;
     extern __shared__ float sw[];
     float *bufA = sw + ((P + 31) / 32) * 32, *bufB = bufA + kH * nthr;
+    const int count = list ? *cnt_ptr : C;
+    // the grid is sized for every cell; blocks past the listed samples leave at once (uniform)
+    if ((int)(blockIdx.x * nthr) >= count) return;
     for (int k = threadIdx.x; k < P; k += blockDim.x) sw[k] = __bfloat162float(wq[k]);
     __syncthreads();
     const float *W1 = sw, *b1 = W1 + DIO * kH, *W2 = b1 + kH, *b2 = W2 + kH * kH, *W3 = b2 + kH, *b3 = W3 + kH * kH,
                 *W4 = b3 + kH, *b4 = W4 + kH * DIO;
     const float *xm = norm, *xs = norm + DIO, *ym = norm + 2 * DIO, *ys = norm + 3 * DIO;
-    const int count = list ? *cnt_ptr : C;
     constexpr int n = DIO + 1;
     const int tid = threadIdx.x;
     // uniform trip count per block so that every thread reaches the same barriers
