@@ -277,7 +277,7 @@ eval_kernel(Tables T, NewtonState S, const double *__restrict__ u, int k, Newton
             const double ez = kexp(z, T.exptab);
             // the ansatz of the trial point: the last accepted trial of a closure leaves the
             // ansatz of its solution behind, so no separate pass is needed
-            if (psi32) psi32[(size_t)cell * Qp + q] = (float)ez;
+            if (psi32) psi32[(size_t)cell * Qp + q] = exp_to_float(ez);
             const double e = wq[q] * ez;
 #pragma unroll
             for (int c = 0; c < n2; ++c) V[c] = fma(e, Mt[c * Qp + q], V[c]);
@@ -342,7 +342,8 @@ sweep64_kernel(Tables T, NewtonState S, int k, double *__restrict__ Vacc, int vs
         const int slot = tile * kSweepThreads + threadIdx.x;
         if (slot >= cnt_in) continue;  // threads are independent: no block barrier below
         const int p_begin = part * sp.units_per_part * 16;
-        const int p_end = min(nunits, (part + 1) * sp.units_per_part) * 16;
+        // padding pairs (w = 0) add nothing: stop at the last real pair
+        const int p_end = min(T.npair, min(nunits, (part + 1) * sp.units_per_part) * 16);
         const int cell = list_in[slot];
         const size_t off = (size_t)cell * n;
         const int ph = S.phase[cell];
@@ -405,7 +406,7 @@ finish_kernel(Tables T, NewtonState S, double *__restrict__ alpha_out, double *_
         double av[n];
 #pragma unroll
         for (int b = 0; b < n; ++b) av[b] = __shfl_sync(kFull, a, b);
-        for (int q = lane; q < Qp; q += 32) {
+        for (int q = lane; q < T.Qf; q += 32) {
             double z = 0.0;
 #pragma unroll
             for (int b = 0; b < n; ++b) z = fma(av[b], T.Mt[b * Qp + q], z);

@@ -280,18 +280,22 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
 #pragma unroll 2
             for (int i = 0; i < kChunk / 4; ++i) {
                 const int pr = c * (kChunk / 2) + h * (kChunk / 4) + i;
-                const int rg = pr < T.npair ? pr / T.P : T.R;
-                if (rg != ring) {
-                    if (ring >= 0)
-                        ring_flush<NN>(T.ringWP + (size_t)ring * n2, B, [&](int cc) -> double & { return U[cc]; });
-                    ring_coeffs<NN>(at, T.ringP + (size_t)rg * n2, A);
-                    ring = rg;
+                // padding pairs (w = 0, warp-uniform) add nothing: their operand is 0 and their
+                // psi stays at the zeros written at allocation
+                const bool real = pr < T.npair;
+                if (real) {
+                    const int rg = pr / T.P;
+                    if (rg != ring) {
+                        if (ring >= 0)
+                            ring_flush<NN>(T.ringWP + (size_t)ring * n2, B, [&](int cc) -> double & { return U[cc]; });
+                        ring_coeffs<NN>(at, T.ringP + (size_t)rg * n2, A);
+                        ring = rg;
+                    }
                 }
                 float f1 = 0.0f, f2 = 0.0f;
-                if (active) {
+                if (active && real) {
                     double e1, e2;
-                    pair_eval<NN, NN>(A, T.ptrig + (size_t)pr * TW, pr < T.npair && pr % T.P == 0,
-                                      T.exptab, B, e1, e2);
+                    pair_eval<NN, NN>(A, T.ptrig + (size_t)pr * TW, pr % T.P == 0, T.exptab, B, e1, e2);
                     f1 = exp_to_float(e1);
                     f2 = exp_to_float(e2);
                     // ansatz of the trial point (the last accepted trial leaves the solution's)

@@ -689,6 +689,11 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
         return KITRT_ECUDA;
     }
     TRY(dev_alloc(mn, &mn->d_psi, C * Qp));
+    // the padding points of psi are never written (their weight is 0): zeros keep them finite
+    if (cudaMemset(mn->d_psi, 0, sizeof(double) * C * Qp) != cudaSuccess) {
+        kitrt_mn_destroy(mn);
+        return KITRT_ECUDA;
+    }
     // sweep work split (sweep.cuh): both sweeps run persistent grids of the CTAs that fit on the
     // SMs at once and split the quadrature of each tile so that every CTA gets several work items
     // (4 for the tensor-core sweep, 2 for the FP64 sweep). A split never needs more than
@@ -705,6 +710,10 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     }
     if (p.mode != KITRT_FP64) {
         TRY(dev_alloc(mn, &mn->d_psi32, C * Qp));
+        if (cudaMemset(mn->d_psi32, 0, sizeof(float) * C * Qp) != cudaSuccess) {
+            kitrt_mn_destroy(mn);
+            return KITRT_ECUDA;
+        }
         TRY(dev_alloc(mn, &mn->d_zero32, (size_t)Qp));
         if (cudaMemset(mn->d_zero32, 0, sizeof(float) * Qp) != cudaSuccess) {
             kitrt_mn_destroy(mn);
