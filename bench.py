@@ -357,6 +357,7 @@ def mode_line(W, r, steps):
             "evaluations_per_cell_step": r["stats"]["evaluations"] / (W["C"] * steps),
             "kernels_ms_per_step": {k: v["total_ms"] / steps for k, v in r["prof"].items()}}
     st = r["stats"]
+    line["fp64_handovers_per_cell_step"] = st.get("handovers", 0) / (W["C"] * steps)
     if st.get("proposals"):
         line["network_proposals_per_cell_step"] = st["proposals"] / (W["C"] * steps)
         line["network_accept_rate"] = 1.0 - st["fallbacks"] / st["proposals"]

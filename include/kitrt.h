@@ -111,6 +111,9 @@ typedef struct {
                               point, stepped from its stored Cholesky factor without a new pass */
     int64_t proposals;     /* KITRT_LEARNED: closures the network was asked for (the rest were
                               already converged from the previous step's state) */
+    int64_t handovers;     /* mixed modes: cells sent from the tensor-core Hessian to the FP64
+                              Hessian (FP32 factor not positive definite, stalled residual, or
+                              line search exhausted), counted once per cell and closure */
 } kitrt_stats;
 
 /* Per-kernel-kind trace record (see kitrt_profile_enable). `units` counts what one kind

@@ -875,7 +875,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
             if (!rc) rc = launch_post(mn, T, mn->st, C, u, k, np, mn->d_Vacc, s);
             if (rc) return rc;
         }
-        CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 11 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaMemcpyAsync(mn->h_cnt, mn->st.cnt, 12 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CUDA_OK(cudaStreamSynchronize(s));
         if (mn->h_cnt[7]) return mn->h_cnt[7];
         int active = mn->h_cnt[k % 3];
@@ -894,6 +894,7 @@ static int run_closure(kitrt_mn *mn, int C, const double *u, const double *alpha
         stats->fallbacks += mn->h_cnt[5];
         stats->restarts += mn->h_cnt[9];
         if (mn->p.mode == KITRT_LEARNED) stats->proposals += mn->h_cnt[8];
+        stats->handovers += mn->h_cnt[11];
     }
     if (mn->h_cnt[3] > 0) {
         // report the first failing code

@@ -89,7 +89,7 @@ struct NewtonState {
                        //   evals, cnt[5] fallbacks, cnt[6] evaluations, cnt[7] timeout status,
                        //   cnt[8] predictor list length, cnt[9] learned-mode steps taken
                        //   from a stored factor, cnt[10] learned-mode residual passes of the
-                       //   network's proposals
+                       //   network's proposals, cnt[11] mixed-mode hand-overs to the FP64 Hessian
 };
 
 struct NewtonParams {

@@ -39,6 +39,16 @@ __device__ __forceinline__ void push(int32_t *list, int32_t *cnt, int cell, int 
     }
 }
 
+// A mixed-mode cell goes over to the FP64 Hessian (FP64 sweep) from the next round on; counted
+// once per cell and closure (S.cnt[11]).
+__device__ __forceinline__ void hand_over(const NewtonState &S, int cell)
+{
+    if (!S.h64[cell]) {
+        S.h64[cell] = 1;
+        atomicAdd(&S.cnt[11], 1);
+    }
+}
+
 __device__ __forceinline__ void fail(const NewtonState &S, int cell, int code, int lane)
 {
     if (lane == 0) {
@@ -134,7 +144,7 @@ __device__ void newton_post(const Tables &T, const NewtonState &S, const NewtonP
         if (h > np.max_halvings && mixed && !S.h64[cell]) {
             // as in newton_post_thread: restart from the accepted point with the FP64 Hessian
             if (lane == 0) {
-                S.h64[cell] = 1;
+                hand_over(S, cell);
                 S.halv[cell] = 0;
                 S.phase[cell] = PH_INIT;
             }
@@ -166,7 +176,7 @@ __device__ void newton_post(const Tables &T, const NewtonState &S, const NewtonP
         __syncwarp();
         if (mixed) {
             // tensor-core rounding broke positive definiteness: redo this point in FP64
-            if (lane == 0) S.h64[cell] = 1;
+            if (lane == 0) hand_over(S, cell);
             push(list_out, cnt_out, cell, lane);
         } else {
             fail(S, cell, KITRT_ECHOL, lane);
@@ -204,7 +214,7 @@ __device__ void newton_post(const Tables &T, const NewtonState &S, const NewtonP
         return;
     }
     if (lane == 0) {
-        if (mixed && ph == PH_NEWTON && gn > kStallRatio * S.gnorm[cell]) S.h64[cell] = 1;
+        if (mixed && ph == PH_NEWTON && gn > kStallRatio * S.gnorm[cell]) hand_over(S, cell);
         if (S.gnorm) S.gnorm[cell] = gn;
         S.gd[cell] = gd;
         S.lam[cell] = 1.0;
@@ -379,7 +389,7 @@ __device__ bool newton_cell(const Tables &T, const NewtonState &S, const NewtonP
             if (h32) {
                 // the line search could not follow the direction from the tensor-core Hessian:
                 // restart from the accepted point with the FP64 Hessian
-                S.h64[cell] = 1;
+                hand_over(S, cell);
                 S.halv[cell] = 0;
                 S.phase[cell] = PH_INIT;
                 return true;
@@ -406,7 +416,7 @@ __device__ bool newton_cell(const Tables &T, const NewtonState &S, const NewtonP
 #pragma unroll
         for (int a = 0; a < n; ++a) yf[(size_t)a * B2] = -d2f_bits(g[a]);
         if (!hess_factor_solve<NN, float>(T, T.gcoef32, np, Vf, B, Lf, yf, B2)) {
-            S.h64[cell] = 1;  // rounding broke positive definiteness: redo this point in FP64
+            hand_over(S, cell);  // rounding broke positive definiteness: redo this point in FP64
             return true;
         }
 #pragma unroll
@@ -455,7 +465,7 @@ __device__ bool newton_cell(const Tables &T, const NewtonState &S, const NewtonP
         fail_t(KITRT_ENOCONVERGE);
         return false;
     }
-    if (mixed && ph == PH_NEWTON && gn > kStallRatio * S.gnorm[cell]) S.h64[cell] = 1;
+    if (mixed && ph == PH_NEWTON && gn > kStallRatio * S.gnorm[cell]) hand_over(S, cell);
     if (S.gnorm) S.gnorm[cell] = gn;
     S.gd[cell] = gd;
     S.lam[cell] = 1.0;

@@ -77,7 +77,7 @@ KITRT_PT_UNROLL
             if (mixed && !S.h64[cell]) {
                 // the line search could not follow the direction from the tensor-core Hessian:
                 // restart from the accepted point with the FP64 Hessian
-                S.h64[cell] = 1;
+                hand_over(S, cell);
                 S.halv[cell] = 0;
                 S.phase[cell] = PH_INIT;
                 return true;
@@ -134,7 +134,7 @@ KITRT_PT_UNROLL
             }
         }
         if (!spd) {
-            S.h64[cell] = 1;  // rounding broke positive definiteness: redo this point in FP64
+            hand_over(S, cell);  // rounding broke positive definiteness: redo this point in FP64
             return true;
         }
         float yf[n];
@@ -238,7 +238,7 @@ KITRT_PT_UNROLL
         fail_t(KITRT_ENOCONVERGE);
         return false;
     }
-    if (mixed && ph == PH_NEWTON && gn > kStallRatio * S.gnorm[cell]) S.h64[cell] = 1;
+    if (mixed && ph == PH_NEWTON && gn > kStallRatio * S.gnorm[cell]) hand_over(S, cell);
     if (S.gnorm) S.gnorm[cell] = gn;
     S.gd[cell] = gd;
     S.lam[cell] = 1.0;

@@ -38,7 +38,8 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("closures", C.c_int64), ("evaluations", C.c_int64), ("max_evals", C.c_int32),
                 ("failed", C.c_int32), ("fallbacks", C.c_int64), ("dt", C.c_double),
-                ("launches", C.c_int64), ("restarts", C.c_int64), ("proposals", C.c_int64)]
+                ("launches", C.c_int64), ("restarts", C.c_int64), ("proposals", C.c_int64),
+                ("handovers", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -217,3 +217,35 @@ def test_m5_million_triangles_sampled_against_oracle(K, mode):
         assert rel_l2(u_gpu[sample], us[pos]) <= 1e-11
     else:
         assert rel_l2(u_gpu[sample, 0], us[pos, 0]) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", MIXED)
+def test_peaked_closures_go_over_to_the_fp64_hessian(K, mode):
+    """Cold closures of strongly peaked densities (vMF lobes up to kappa = 400, near the
+    realizability boundary, where the Hessian is ill-conditioned): part of the cells leave the
+    tensor-core Hessian for the FP64 one (FP32 factor not positive definite, or a stalled
+    residual), are evaluated by the FP64 sweep, and have their FP64 quadrature parts summed in
+    FP64. Every closure that the oracle solves is solved, to the same moments and alpha."""
+    N, order = 3, 20
+    T = O.Tables(N, order)
+    m = synth.jittered_mesh(20, 0.0, 1.0, seed=4)
+    mesh = K.Mesh(m.xy, m.tri)
+    C = mesh.ncells
+    s = K.MNSolver(mesh, N, order, mode=mode, tau=1e-10)
+    u = vmf_u(T, C, seed=77, kappa_hi=400.0)
+    a_or = O.isotropic_alpha(T, u)
+    st_or, _ = O.closure(T, u, a_or)
+    ud = dev(u)
+    ad = s.isotropic_alpha(ud)
+    st = torch.zeros(C, dtype=torch.int32, device="cuda")
+    rc, stats = s.closure(ud, ad, st, stats=True, check=False)
+    print(mode, "hand-overs", stats["handovers"], "of", C, "cells; evaluations", stats["evaluations"])
+    assert stats["handovers"] > 0
+    st = st.cpu().numpy()
+    ok = (st == 0) & (st_or == 0)
+    assert ((st == 0) == (st_or == 0)).mean() > 0.98
+    assert ok.mean() > 0.9
+    a_gpu = ad.cpu().numpy()
+    rec = np.exp(a_gpu[ok] @ T.M.T) @ (T.w[:, None] * T.M)
+    rel = np.linalg.norm(rec - u[ok], axis=1) / np.linalg.norm(u[ok], axis=1)
+    assert rel.max() <= 1e-9
