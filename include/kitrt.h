@@ -385,6 +385,11 @@ int32_t kitrt_gather_rows(const double *src, const int32_t *idx, int32_t count, 
 /* dst row idx[k] = src [count x width] row k. */
 int32_t kitrt_scatter_rows(const double *src, const int32_t *idx, int32_t count, int32_t width,
                            double *dst, void *stream);
+/* dst row idx[k] += src [count x width] row k: the adjoint's reverse halo (the transpose of the
+ * halo exchange), adding the contributions other ranks computed for this rank's cells. The
+ * indices of one call must be distinct. */
+int32_t kitrt_scatter_add_rows(const double *src, const int32_t *idx, int32_t count, int32_t width,
+                               double *dst, void *stream);
 
 /* ---- Learned closure [Sec. 3.1: neural entropy closures replace the Newton solve] --------------
  * A plain MLP with three softplus hidden layers maps the normalised moments v = u_{1..n-1}/u_0

@@ -102,6 +102,7 @@ SIGNATURES = {
                                   C.c_int32, _vp]),
     "kitrt_gather_rows": (C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp]),
     "kitrt_scatter_rows": (C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp]),
+    "kitrt_scatter_add_rows": (C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp]),
     "kitrt_profile_enable": (C.c_int32, [_vp, C.c_int32]),
     "kitrt_profile_read": (C.c_int32, [_vp, C.POINTER(ProfileEntry), C.c_int32, _ip]),
 }
@@ -404,6 +405,15 @@ def scatter_rows(src, idx, dst):
     _check(_lib().kitrt_scatter_rows(_dev(src, torch.float64), _dev(idx, torch.int32), int(idx.numel()),
                                      int(dst.shape[1]), _dev(dst, torch.float64), _stream()),
            "kitrt_scatter_rows")
+
+
+def scatter_add_rows(src, idx, dst):
+    """dst[idx[k]] += src[k] (FP64 CUDA tensors, idx int32 CUDA with distinct entries)."""
+    import torch
+    _check(_lib().kitrt_scatter_add_rows(_dev(src, torch.float64), _dev(idx, torch.int32),
+                                         int(idx.numel()), int(src.shape[1]),
+                                         _dev(dst, torch.float64), _stream()),
+           "kitrt_scatter_add_rows")
 
 
 # ---- MLP kernels of the learned closure -------------------------------------------------------

@@ -47,8 +47,18 @@ def training_data(solver: "kitrt.MNSolver", count: int, seed: int, kappa_hi: flo
     return u[ok].contiguous(), alpha[ok].contiguous()
 
 
+def allreduce_mean(t, dist):
+    """Data-parallel training over ranks: the mean over the ranks of a gradient (or loss) tensor,
+    in place. Every rank computes the gradient of its equal share of a batch; the loss being a
+    mean over samples, the mean of the shares' gradients is the whole batch's gradient, so the
+    ranks take identical Adam steps from identical parameters."""
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    t /= dist.get_world_size()
+    return t
+
+
 def train(u, alpha, hidden: int = 64, epochs: int = 30, batch: int = 1024, lr: float = 3e-3,
-          seed: int = 0, log_every: int = 0) -> TrainedMLP:
+          seed: int = 0, log_every: int = 0, dist=None) -> TrainedMLP:
     import torch
     n = u.shape[1]
     din = dout = n - 1
@@ -82,8 +92,13 @@ def train(u, alpha, hidden: int = 64, epochs: int = 30, batch: int = 1024, lr: f
         ep_loss = torch.zeros((), device=params.device)
         for b in range(nb):
             idx = perm[b * batch:(b + 1) * batch]
+            if dist is not None:  # this rank's share of the batch (same permutation on every rank)
+                idx = idx[dist.get_rank()::dist.get_world_size()]
             xb, yb = X[idx].contiguous(), Y[idx].contiguous()
             loss, grad = kitrt.mlp_loss_grad(params, xb, yb, din, hidden, dout, work=work)
+            if dist is not None:
+                allreduce_mean(grad, dist)
+                allreduce_mean(loss, dist)
             t += 1
             kitrt.mlp_adam(params, grad, m, v, t, lr=lr_ep)
             ep_loss += loss[0]

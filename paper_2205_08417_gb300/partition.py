@@ -16,10 +16,15 @@ Exchanging alpha as well keeps every halo closure on its owner's Newton start: t
 cells' second-stage inputs are not exact, and a Newton iterate depends on its start at the
 rounding level, so without it the owned cells would match the single-rank step only to the
 closure tolerance.
+The discrete adjoint runs the transposed map: a rank applies the transposed step to its owned
+cells' adjoint rows (zero on its halo), which leaves contributions on its halo rows that belong to
+the owners of those cells; reverse_exchange sends them back and adds them there (the transpose of
+the forward exchange: a gather becomes a scatter-add).
 This module holds only the host-side bookkeeping (partition, local mesh, send and receive lists)
-and the exchange's sequencing; the rows are packed and unpacked by callables the caller passes
-(kitrt.gather_rows / kitrt.scatter_rows for device arrays) and moved with torch.distributed
-point-to-point operations (NCCL between GPUs; gloo between CPU processes in the tests).
+and the exchanges' sequencing; the rows are packed and unpacked by callables the caller passes
+(kitrt.gather_rows / kitrt.scatter_rows / kitrt.scatter_add_rows for device arrays) and moved with
+torch.distributed point-to-point operations (NCCL between GPUs; gloo between CPU processes in the
+tests).
 """
 from __future__ import annotations
 
@@ -111,3 +116,22 @@ class Partition:
             q.wait()
         for r, idx in sorted(self.recv.items()):
             unpack(inbox[r], idx, u)
+
+    def reverse_exchange(self, v, pack, unpack_add, empty, dist):
+        """Transpose of exchange(): send the halo rows of a local per-cell array v (contributions of
+        this rank's owned rows to cells other ranks own) to their owners, and add the rows received
+        for this rank's cells into v. pack(v, idx) returns rows idx of v as a contiguous buffer,
+        unpack_add(buf, idx, v) adds buffer row k to row idx[k] of v, empty(k) makes a receive
+        buffer. All ranks call it together; the received rows are added in increasing rank order.
+        The halo rows of v are left as they were (the caller zeroes them if it reuses v)."""
+        reqs, inbox, outbox = [], {}, []
+        for r, idx in sorted(self.recv.items()):
+            outbox.append(pack(v, idx))
+            reqs.append(dist.isend(outbox[-1], r))
+        for r, idx in sorted(self.send.items()):
+            inbox[r] = empty(idx.size)
+            reqs.append(dist.irecv(inbox[r], r))
+        for q in reqs:
+            q.wait()
+        for r, idx in sorted(self.send.items()):
+            unpack_add(inbox[r], idx, v)

@@ -98,3 +98,12 @@ def test_row_kernels_gather_and_scatter(K):
     ref = np.zeros((50, 7))
     ref[idx] = src[idx]
     np.testing.assert_array_equal(dst.cpu().numpy(), ref)
+    # scatter-add (the adjoint's reverse halo): rows idx gain the buffer's rows, the others keep theirs
+    base = rng.normal(size=(50, 7))
+    acc = dev(base)
+    K.scatter_add_rows(out, dev(idx), acc)
+    ref = base.copy()
+    ref[idx] += src[idx]
+    np.testing.assert_array_equal(acc.cpu().numpy(), ref)
+    K.scatter_add_rows(out[:0], dev(idx[:0]), acc)  # an empty batch changes nothing
+    np.testing.assert_array_equal(acc.cpu().numpy(), ref)

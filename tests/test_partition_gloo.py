@@ -122,3 +122,77 @@ def test_partition_bookkeeping():
     h1 = halo_cells(G.nbr, 0, 50, 1)
     h2 = halo_cells(G.nbr, 0, 50, 2)
     assert np.array_equal(h2[:h1.size], h1) and h2.size > h1.size
+
+
+def _vjp_state():
+    """A line-source state after a few oracle steps, its closure, and a seeded adjoint row set."""
+    import oracle as O
+    m, G, T, u0, sa, ss, q = _problem()
+    dt = G.cfl_dt(0.3)
+    u = u0.copy()
+    a = O.isotropic_alpha(T, u)
+    for _ in range(3):
+        _run(O, T, G, u, a, sa, ss, q, dt, 1)
+    st, _ = O.closure(T, u, a)
+    assert (st == 0).all()
+    lam = np.random.default_rng(11).normal(size=u.shape)
+    return m, G, T, u, a, sa, ss, dt, lam
+
+
+def _rank_vjp(rank, world, port, out):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch.distributed as dist
+    import oracle as O
+    from paper_2205_08417_gb300.partition import Partition
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        m, G, T, u, a, sa, ss, dt, lam = _vjp_state()
+        part = Partition(m.xy, m.tri, G.nbr, rank, world, layers=1)
+        Gl = O.Geometry(part.xy, part.tri)
+        # the linearisation point on the local cells; adjoint rows of the owned cells only
+        ul, al = part.local(u), part.local(a)
+        laml = part.local(lam)
+        laml[part.n_owned:] = 0.0
+        v = O.step_vjp(T, Gl, ul, al, part.local(sa), part.local(ss), dt, laml)
+        n = T.n
+        pack = lambda vv, idx: torch.from_numpy(np.ascontiguousarray(vv[idx]))
+        def unpack_add(buf, idx, vv):
+            vv[idx] += buf.numpy()
+        empty = lambda k: torch.empty((k, n), dtype=torch.float64)
+        before = v[:part.n_owned].copy()
+        part.reverse_exchange(v, pack, unpack_add, empty, dist)
+        out.put((rank, part.lo, part.hi, v[:part.n_owned].copy(), before))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_adjoint_step_with_the_reverse_halo():
+    """The transposed step split over two ranks: each applies the oracle's one-step transpose on
+    its local mesh to its owned adjoint rows (zero on the halo) and sends the halo rows' results
+    back to their owners, which add them (the reverse halo of the adjoint). The owned rows equal
+    the single-rank transposed step to round-off (the additions come in another order)."""
+    import oracle as O
+    m, G, T, u, a, sa, ss, dt, lam = _vjp_state()
+    ref = O.step_vjp(T, G, u, a, sa, ss, dt, lam)
+    ctx = torch.multiprocessing.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_vjp, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [out.get(timeout=300) for _ in procs]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = np.zeros_like(ref)
+    local_only = np.zeros_like(ref)
+    for rank, lo, hi, vo, before in res:
+        got[lo:hi] = vo
+        local_only[lo:hi] = before
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    # without the reverse halo the cells next to the cut miss their neighbours' terms
+    assert np.abs(local_only - ref).max() > 1e-3 * np.abs(ref).max()
