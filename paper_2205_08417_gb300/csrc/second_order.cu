@@ -17,11 +17,12 @@
 // with base = u^n, in = u*.
 // Kernels: warp per cell, lanes over the folded quadrature points; FP64 (FP64 mode) or FP32
 // ordinates and arithmetic with an FP64 update (mixed modes, as the first-order FP32 flux).
+#include "flux_group.cuh"
 #include "kitrt_internal.cuh"
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using kitrt_flux::kFull;
 constexpr int kWarps = 8;
 
 template <typename P>
@@ -87,6 +88,93 @@ recon_kernel(int Qp, const int4 *__restrict__ nbr, const P *__restrict__ nrm,
             const P L = num < den ? num / den : P(1);
 #pragma unroll
             for (int f = 0; f < 3; ++f) psif[((size_t)i * 3 + f) * Qp + q] = pi + L * D[f];
+        }
+    }
+}
+
+// FP32 reconstruction of the mixed modes, laid out as the FP32 fluxes: a group of 8 lanes per
+// cell, 4 cells per warp, 16-byte pieces (4 consecutive points) of the cell's row and of its
+// neighbours' rows (on the boundary the cell's own row, Neumann, or the zero row, vacuum), the
+// same arithmetic as recon_kernel per point, the three face values stored as 16-byte pieces.
+__global__ void __launch_bounds__(kWarps * 32)
+recon32_kernel(int Qp, const int4 *__restrict__ nbr, const float *__restrict__ nrm,
+               const float *__restrict__ r, const float *__restrict__ inva,
+               const float *__restrict__ psi, const float *__restrict__ zrow,
+               float *__restrict__ psif, int bc, int C)
+{
+    using namespace kitrt_flux;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane >> kGroupLog, gl = lane & (kGroup - 1);
+    const int nq4 = Qp / 4;
+    for (int b0 = (blockIdx.x * kWarps + wib) * kCellsPerWarp; b0 < C;
+         b0 += gridDim.x * kWarps * kCellsPerWarp) {
+        const int i = b0 + grp;
+        if (i >= C) continue;  // no warp-collective operation below
+        const int4 nb = nbr[i];
+        const int j[3] = {nb.x, nb.y, nb.z};
+        float nx[3], ny[3], rx[3], ry[3];
+        const float4 *own = reinterpret_cast<const float4 *>(psi + (size_t)i * Qp);
+        const float4 *nrow[3];
+        float4 *frow[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            nx[f] = nrm[6 * (size_t)i + 2 * f];
+            ny[f] = nrm[6 * (size_t)i + 2 * f + 1];
+            rx[f] = r[6 * (size_t)i + 2 * f];
+            ry[f] = r[6 * (size_t)i + 2 * f + 1];
+            nrow[f] = j[f] >= 0 ? reinterpret_cast<const float4 *>(psi + (size_t)j[f] * Qp)
+                      : bc == 0 ? own
+                                : reinterpret_cast<const float4 *>(zrow);
+            frow[f] = reinterpret_cast<float4 *>(psif + ((size_t)i * 3 + f) * Qp);
+        }
+        const float half_inva = 0.5f * inva[i];
+#pragma unroll 1
+        for (int q4 = gl; q4 < nq4; q4 += kGroup) {
+            const float4 p4 = __ldg(own + q4);
+            float4 n4[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) n4[f] = __ldg(nrow[f] + q4);
+            float out[3][4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float pi = c == 0 ? p4.x : c == 1 ? p4.y : c == 2 ? p4.z : p4.w;
+                float pj[3];
+#pragma unroll
+                for (int f = 0; f < 3; ++f)
+                    pj[f] = c == 0 ? n4[f].x : c == 1 ? n4[f].y : c == 2 ? n4[f].z : n4[f].w;
+                float gx = 0.0f, gy = 0.0f;
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const float sf = pi + pj[f];
+                    gx += sf * nx[f];
+                    gy += sf * ny[f];
+                }
+                gx *= half_inva;
+                gy *= half_inva;
+                // the smallest ratio bound / D over the faces, kept as a fraction, divided once
+                float num = 1.0f, den = 1.0f, D[3];
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    D[f] = gx * rx[f] + gy * ry[f];
+                    float a = 0.0f, b = 0.0f;
+                    if (D[f] > 0.0f) {
+                        a = (pi > pj[f] ? pi : pj[f]) - pi;
+                        b = D[f];
+                    } else if (D[f] < 0.0f) {
+                        a = pi - (pi < pj[f] ? pi : pj[f]);
+                        b = -D[f];
+                    }
+                    if (b > 0.0f && a * den < num * b) {
+                        num = a;
+                        den = b;
+                    }
+                }
+                const float L = num < den ? num / den : 1.0f;
+#pragma unroll
+                for (int f = 0; f < 3; ++f) out[f][c] = pi + L * D[f];
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f) frow[f][q4] = make_float4(out[f][0], out[f][1], out[f][2], out[f][3]);
         }
     }
 }
@@ -160,98 +248,113 @@ flux2_kernel(Tables T, const int4 *__restrict__ nbr, const double *__restrict__ 
     }
 }
 
-// FP32 variant for the mixed modes: FP32 ordinates, face values and sums, a compensated warp
-// reduction, the increment in FP32 and the Heun combination in FP64 (lanes over the elements of a
-// batch of cells, as in the first-order FP32 flux).
-constexpr int kBatch = 4;
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    const float bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
-}
-
+// FP32 variant for the mixed modes: FP32 ordinates, face values and sums, the increment in FP32
+// and the Heun combination in FP64. Layout as the first-order FP32 flux (flux_group.cuh): a group
+// of 8 lanes per cell, 4 cells per warp, 16-byte pieces (4 consecutive points) of the cell's row,
+// of its three face rows and of the three upwind face rows, the group's lane sums reduced with a
+// compensated reduce-scatter, then lanes over the (cell, moment) elements of the warp's cells.
 template <int NN>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, NN <= 3 ? 3 : 2)
 flux2_32_kernel(Tables T, const int4 *__restrict__ nbr, const float *__restrict__ nrm32,
                 const float *__restrict__ inva32, const float *__restrict__ psi,
-                const float *__restrict__ psif, const double *__restrict__ uin,
-                const double *__restrict__ base, double *__restrict__ uout,
-                const double *__restrict__ sa, const double *__restrict__ ss,
-                const double *__restrict__ qs, float dt, double c0, double c1, int bc, int C)
+                const float *__restrict__ psif, const float *__restrict__ zrow,
+                const double *__restrict__ uin, const double *__restrict__ base,
+                double *__restrict__ uout, const double *__restrict__ sa,
+                const double *__restrict__ ss, const double *__restrict__ qs, float dt, double c0,
+                double c1, int bc, int C)
 {
+    using namespace kitrt_flux;
     constexpr int n = (NN + 1) * (NN + 2) / 2;
-    __shared__ float sF[kWarps][kBatch * n];
-    __shared__ float sK[kWarps][kBatch][4];  // per cell: sigma_a, sigma_s, q, 1/A
+    constexpr int K = GroupRS<n>::K;
+    __shared__ float sF[kWarps][kCellsPerWarp * n];
+    __shared__ float sK[kWarps][kCellsPerWarp][4];  // per cell: sigma_a, sigma_s, q, 1/A
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int Qp = T.Qp;
-    for (int b0 = (blockIdx.x * kWarps + wib) * kBatch; b0 < C; b0 += gridDim.x * kWarps * kBatch) {
-        const int nb_cells = C - b0 < kBatch ? C - b0 : kBatch;
+    const int grp = lane >> kGroupLog, gl = lane & (kGroup - 1);
+    const int Qp = T.Qp, nq4 = Qp / 4;
+    const float4 *__restrict__ wx4 = reinterpret_cast<const float4 *>(T.wox32);
+    const float4 *__restrict__ wy4 = reinterpret_cast<const float4 *>(T.woy32);
+    const float4 *__restrict__ M4 = reinterpret_cast<const float4 *>(T.Mt32);
+    for (int b0 = (blockIdx.x * kWarps + wib) * kCellsPerWarp; b0 < C;
+         b0 += gridDim.x * kWarps * kCellsPerWarp) {
+        const int nb_cells = C - b0 < kCellsPerWarp ? C - b0 : kCellsPerWarp;
         if (lane < 4 * nb_cells) {
             const int ci = lane >> 2, which = lane & 3, i = b0 + ci;
             const double v = which == 0 ? sa[i] : which == 1 ? ss[i] : qs[i];
             sK[wib][ci][which] = which == 3 ? inva32[i] : (float)v;
         }
-        for (int ci = 0; ci < nb_cells; ++ci) {
-            const int i = b0 + ci;
-            const int4 nb = nbr[i];
-            const int j[3] = {nb.x, nb.y, nb.z};
-            const int kk[3] = {nb.w & 3, (nb.w >> 2) & 3, (nb.w >> 4) & 3};
-            float nx[3], ny[3];
+        // a group without a cell repeats the warp's last one; its sums are not stored
+        const int i = b0 + (grp < nb_cells ? grp : nb_cells - 1);
+        const int4 nb = nbr[i];
+        const int j[3] = {nb.x, nb.y, nb.z};
+        const int kk[3] = {nb.w & 3, (nb.w >> 2) & 3, (nb.w >> 4) & 3};
+        float nx[3], ny[3];
+        const float4 *own = reinterpret_cast<const float4 *>(psi + (size_t)i * Qp);
+        const float4 *ofr[3], *ufr[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            nx[f] = nrm32[6 * (size_t)i + 2 * f];
+            ny[f] = nrm32[6 * (size_t)i + 2 * f + 1];
+            ofr[f] = reinterpret_cast<const float4 *>(psif + ((size_t)i * 3 + f) * Qp);
+            // upwind face value: the neighbour's at the shared face; across a boundary the
+            // cell's own face value (Neumann) or zero (vacuum)
+            ufr[f] = j[f] >= 0 ? reinterpret_cast<const float4 *>(psif + ((size_t)j[f] * 3 + kk[f]) * Qp)
+                     : bc == 0 ? ofr[f]
+                               : reinterpret_cast<const float4 *>(zrow);
+        }
+        float F[n];
+#pragma unroll
+        for (int a = 0; a < n; ++a) F[a] = 0.0f;
+#pragma unroll 1
+        for (int q4 = gl; q4 < nq4; q4 += kGroup) {
+            const float4 po = __ldg(own + q4);
+            const float4 wx = __ldg(wx4 + q4), wy = __ldg(wy4 + q4);
+            float4 of[3], uf[3];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                nx[f] = nrm32[6 * (size_t)i + 2 * f];
-                ny[f] = nrm32[6 * (size_t)i + 2 * f + 1];
+                of[f] = __ldg(ofr[f] + q4);
+                uf[f] = __ldg(ufr[f] + q4);
             }
-            float F[n];
+            float sv[4];
 #pragma unroll
-            for (int a = 0; a < n; ++a) F[a] = 0.0f;
-#pragma unroll 2
-            for (int q = lane; q < Qp; q += 32) {
-                const float pi = __ldg(psi + (size_t)i * Qp + q);
-                const float wx = T.wox32[q], wy = T.woy32[q];
-                float s = 0.0f;
+            for (int c = 0; c < 4; ++c) {
+                const float pi = c == 0 ? po.x : c == 1 ? po.y : c == 2 ? po.z : po.w;
+                const float wxc = c == 0 ? wx.x : c == 1 ? wx.y : c == 2 ? wx.z : wx.w;
+                const float wyc = c == 0 ? wy.x : c == 1 ? wy.y : c == 2 ? wy.z : wy.w;
+                float acc = 0.0f;
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
-                    const float d = fmaf(wx, nx[f], wy * ny[f]);
-                    const float own = __ldg(psif + ((size_t)i * 3 + f) * Qp + q);
-                    // the neighbour's face value is loaded unconditionally (own row as a stand-in
-                    // across a boundary) so that all loads of a point are in flight together
-                    const size_t jrow = j[f] >= 0 ? ((size_t)j[f] * 3 + kk[f]) : ((size_t)i * 3 + f);
-                    const float nbv = __ldg(psif + jrow * Qp + q);
-                    const float up = d > 0.0f ? own : (j[f] >= 0 ? nbv : (bc == 0 ? own : 0.0f));
-                    s = fmaf(d, up - pi, s);
+                    const float o = c == 0 ? of[f].x : c == 1 ? of[f].y : c == 2 ? of[f].z : of[f].w;
+                    const float uu = c == 0 ? uf[f].x : c == 1 ? uf[f].y : c == 2 ? uf[f].z : uf[f].w;
+                    const float d = fmaf(wxc, nx[f], wyc * ny[f]);
+                    acc = fmaf(d, (d > 0.0f ? o : uu) - pi, acc);
                 }
-#pragma unroll
-                for (int a = 0; a < n; ++a) F[a] = fmaf(T.Mt32[a * Qp + q], s, F[a]);
+                sv[c] = acc;
             }
-            // compensated reduction of the 32 lane sums (butterfly of two-sums)
 #pragma unroll
             for (int a = 0; a < n; ++a) {
-                float sv = F[a], ev = 0.0f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float so = __shfl_xor_sync(kFull, sv, o), eo = __shfl_xor_sync(kFull, ev, o);
-                    float t, e;
-                    two_sum(sv, so, t, e);
-                    sv = t;
-                    ev = ev + eo + e;
-                }
-                if (lane == 0) sF[wib][ci * n + a] = sv + ev;
+                const float4 m = __ldg(M4 + (size_t)a * nq4 + q4);
+                F[a] = fmaf(m.w, sv[3], fmaf(m.z, sv[2], fmaf(m.y, sv[1], fmaf(m.x, sv[0], F[a]))));
             }
+        }
+        float rs[K], re[K];
+        int slot0;
+        const bool uniq = group_reduce_scatter<n>(F, gl, rs, re, slot0);
+        if (grp < nb_cells && uniq) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (slot0 + k < n) sF[wib][grp * n + slot0 + k] = rs[k] + re[k];
         }
         __syncwarp();
         for (int idx = lane; idx < nb_cells * n; idx += 32) {
-            const int ci = idx / n, a = idx - ci * n, i = b0 + ci;
-            const double ua = uin[(size_t)i * n + a];
+            const int ci = idx / n, a = idx - ci * n, ic = b0 + ci;
+            const double ua = uin[(size_t)ic * n + a];
             const float *k = sK[wib][ci];
             const float sig = a == 0 ? k[0] : k[0] + k[1];
             const float R = fmaf(-sig, (float)ua, k[2] * T.mbar32[a]);
             const float inc = dt * fmaf(-k[3], sF[wib][idx], R);
             const double next = ua + (double)inc;
-            const double b = c0 != 0.0 ? base[(size_t)i * n + a] : 0.0;
-            uout[(size_t)i * n + a] = c0 * b + c1 * next;
+            const double b = c0 != 0.0 ? base[(size_t)ic * n + a] : 0.0;
+            uout[(size_t)ic * n + a] = c0 * b + c1 * next;
         }
         __syncwarp();
     }
@@ -267,11 +370,15 @@ int launch_recon(kitrt_mn *mn, const Tables &T, const void *psi, void *psif, boo
     int blocks = (C + kWarps - 1) / kWarps;
     if (blocks > mn->nsm * 16) blocks = mn->nsm * 16;
     LaunchScope ls(mn, PK_RECON, s, C);
-    if (fp32)
-        recon_kernel<float><<<blocks, kWarps * 32, 0, s>>>(T.Qp, m->d_nbr, m->d_nrm32, m->d_r32,
-                                                           m->d_inva32, (const float *)psi,
-                                                           (float *)psif, bc, C);
-    else
+    if (fp32) {
+        if (T.Qp % 32 != 0 || !mn->d_zero32) return KITRT_EINVAL;
+        const int cells_per_block = kWarps * kitrt_flux::kCellsPerWarp;
+        int blocks32 = (C + cells_per_block - 1) / cells_per_block;
+        if (blocks32 > mn->nsm * 8) blocks32 = mn->nsm * 8;
+        recon32_kernel<<<blocks32, kWarps * 32, 0, s>>>(T.Qp, m->d_nbr, m->d_nrm32, m->d_r32,
+                                                       m->d_inva32, (const float *)psi,
+                                                       mn->d_zero32, (float *)psif, bc, C);
+    } else
         recon_kernel<double><<<blocks, kWarps * 32, 0, s>>>(T.Qp, m->d_nbr, m->d_nrm, m->d_r,
                                                             m->d_inva, (const double *)psi,
                                                             (double *)psif, bc, C);
@@ -287,15 +394,17 @@ int launch_flux2(kitrt_mn *mn, const Tables &T, const void *psi, const void *psi
     const int C = m->C;
     int blocks = (C + kWarps - 1) / kWarps;
     if (blocks > mn->nsm * 16) blocks = mn->nsm * 16;
-    int blocks32 = (C + kWarps * kBatch - 1) / (kWarps * kBatch);
-    if (blocks32 > mn->nsm * 8) blocks32 = mn->nsm * 8;
+    if (fp32 && (T.Qp % 32 != 0 || !mn->d_zero32)) return KITRT_EINVAL;
+    const int cells_per_block = kWarps * kitrt_flux::kCellsPerWarp;
+    int blocks32 = (C + cells_per_block - 1) / cells_per_block;
+    if (blocks32 > mn->nsm * 3) blocks32 = mn->nsm * 3;  // persistent: the CTAs resident at once
     LaunchScope ls(mn, PK_FLUX, s, C);
 #define FLUX2_CASE(NNv)                                                                           \
     case NNv:                                                                                     \
         if (fp32)                                                                                 \
             flux2_32_kernel<NNv><<<blocks32, kWarps * 32, 0, s>>>(                                \
                 T, m->d_nbr, m->d_nrm32, m->d_inva32, (const float *)psi, (const float *)psif,    \
-                uin, base, uout, sa, ss, q, (float)dt, c0, c1, bc, C);                            \
+                mn->d_zero32, uin, base, uout, sa, ss, q, (float)dt, c0, c1, bc, C);              \
         else                                                                                      \
             flux2_kernel<NNv><<<blocks, kWarps * 32, 0, s>>>(                                     \
                 T, m->d_nbr, m->d_nrm, m->d_inva, (const double *)psi, (const double *)psif, uin, \
