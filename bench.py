@@ -647,7 +647,8 @@ def main():
                      "peak_source": "FP64 pipe: measured cuBLAS DGEMM 4096^3 in this run "
                                     f"({peak:.3f} TFLOP/s) / 2 flops per FMA instruction; achieved "
                                     "counts the sweep's FP64 instructions per cell evaluation "
-                                    "(sum-factorised exponent and moments, 8 per exp) x evaluations "
+                                    "(sum-factorised exponent and moments; 2 per exp in the mixed "
+                                    "modes, 8 in FP64 mode) x evaluations "
                                     "/ the sweep's CUDA-event time",
                      "fp64_ops_per_cell_eval": ops,
                      "fp64_flops_per_cell_eval": fl,

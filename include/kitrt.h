@@ -175,7 +175,9 @@ int32_t kitrt_mn_sizes(const kitrt_mn *mn, int32_t *nmom, int32_t *nquad, int32_
  *                      moments run on tensor cores; L = 2N in FP64 mode), per ring the exponent
  *                      coefficients (n FMA) and the moments (nmom(L) FMA);
  *   sweep_fp64_ops     FP64-pipe instructions of the same sweep including the exponentials
- *                      (8 per exp on the common path of the table-driven method);
+ *                      (on the common path of the table-driven method: 8 per exp in FP64
+ *                      mode; 2 in the mixed modes, whose exponents are pre-scaled by 2048/ln2
+ *                      and whose small polynomial term is formed in FP32);
  *   exps               exponentials per evaluation (Q');
  *   tensor_flops       mixed modes: 3 x 2 (n2 - n) Q' on tensor cores (three split products);
  *   newton_flops       the per-cell Newton step: 2 nnz (Hessian) + n^3/3 + 2n^2 (Cholesky,

@@ -261,6 +261,9 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                     at[a] = ph == PH_NEWTON ? fma(lam, S.dir[(size_t)cell * n + a], al) : al;
                 }
             }
+            // the pairs take the exponent in units of ln2/2048 (kexp_scaled)
+#pragma unroll
+            for (int a = 0; a < n; ++a) at[a] *= 2954.639443740597;  // 2048 / ln2
         }
         int ring = -1;  // ring whose azimuthal sums B holds (uniform within a warp)
         for (int c = c_begin; c < c_end; ++c) {
@@ -295,7 +298,7 @@ eval_mixed_kernel(Tables T, NewtonState S, int k, const void *__restrict__ Mhi,
                 float f1 = 0.0f, f2 = 0.0f;
                 if (active && real) {
                     double e1, e2;
-                    pair_eval<NN, NN>(A, T.ptrig + (size_t)pr * TW, pr % T.P == 0, T.exptab, B, e1, e2);
+                    pair_eval<NN, NN, true>(A, T.ptrig + (size_t)pr * TW, pr % T.P == 0, T.exptab, B, e1, e2);
                     f1 = exp_to_float(e1);
                     f2 = exp_to_float(e2);
                     // ansatz of the trial point (the last accepted trial leaves the solution's)

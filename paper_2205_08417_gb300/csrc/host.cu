@@ -624,9 +624,14 @@ int32_t kitrt_mn_init(const kitrt_mesh *mesh, const kitrt_mn_params *params, kit
     TRY(dev_upload(mn, &mn->d_oy, oyp));
     TRY(dev_upload(mn, &mn->d_ox32, oxp32));
     TRY(dev_upload(mn, &mn->d_oy32, oyp32));
-    // 2^(j/2048), j = 0..2047, rounded to double from extended precision
-    std::vector<double> exptab(2048);
-    for (int j = 0; j < 2048; ++j) exptab[j] = (double)exp2l((long double)j / 2048.0L);
+    // 2^(j/2048), j = 0..2047, then 2^(j/2048) ln2/2048 (kexp_scaled), rounded to double from
+    // extended precision
+    std::vector<double> exptab(4096);
+    for (int j = 0; j < 2048; ++j) {
+        const long double t = exp2l((long double)j / 2048.0L);
+        exptab[j] = (double)t;
+        exptab[2048 + j] = (double)(t * (logl(2.0L) / 2048.0L));
+    }
     TRY(dev_upload(mn, &mn->d_exptab, exptab));
     // sum-factorised sweeps: azimuthal factors per pair and Legendre factors per ring
     {
@@ -792,7 +797,7 @@ int32_t kitrt_mn_work(const kitrt_mn *mn, kitrt_work *out)
     const double pair_ops = N + N + 2 + 2 + 1 + 2 * L, pair_fmas = N + (N - 1) + 2 * L;
     const double ring_fmas = n + nout;
     out->sweep_fp64_flops = pairs * (pair_ops + pair_fmas) + rings * 2 * ring_fmas;
-    out->sweep_fp64_ops = pairs * pair_ops + rings * ring_fmas + Qf * kExpFp64Ops;
+    out->sweep_fp64_ops = pairs * pair_ops + rings * ring_fmas + Qf * (fp64 ? kExpFp64Ops : kExpScaledFp64Ops);
     out->exps = Qf;
     out->tensor_flops = fp64 ? 0.0 : 3.0 * 2.0 * (n2 - n) * Qf;
     out->newton_flops = 2.0 * mn->gaunt_nnz + n * n * n / 3 + 2 * n * n;

@@ -19,6 +19,9 @@
 // FP64-pipe instructions of one kexp on its common path (kexp.cuh): 2 for the rounding to the
 // table index, 2 for the two-part reduction, 3 for the polynomial, 1 for the table scaling.
 constexpr int kExpFp64Ops = 8;
+// FP64-pipe instructions of one kexp_scaled (sweep.cuh, the mixed sweep): r = s - k and the
+// final fused multiply-add.
+constexpr int kExpScaledFp64Ops = 2;
 
 // Per-cell Newton phase.
 enum : int32_t { PH_DONE = 0, PH_INIT = 1, PH_NEWTON = 2 };
@@ -58,7 +61,7 @@ struct Tables {
     const float *w32;
     const float *wox32, *woy32;  // FP32 copies of w * Omega
     const float *mbar32;         // [n] FP32 copy of <m>
-    const double *exptab;     // [2048] 2^(j/2048) for kexp
+    const double *exptab;     // [2 x 2048] 2^(j/2048) (kexp), then 2^(j/2048) ln2/2048 (kexp_scaled)
     // sum-factorised sweeps (sweep.cuh): rings of P pairs of points; R rings (row R of the ring
     // tables is zero, for padding pairs); npair = Qf / 2 pairs
     int R, P, npair;
@@ -136,7 +139,7 @@ struct kitrt_mn {
     int grid_mixed = 0, grid_fp64 = 0;      // persistent grids of the sweeps
     int R = 0, P = 0;                    // rings and pairs per ring of the folded rule
     double *d_ptrig = nullptr, *d_ringP = nullptr, *d_ringWP = nullptr;
-    double *d_exptab = nullptr;          // [2048] 2^(j/2048)
+    double *d_exptab = nullptr;          // [2 x 2048] exp tables (Tables::exptab)
     void *d_mlp16 = nullptr;             // learned closure: BF16 network parameters
     float *d_mlp_norm = nullptr;         // [4 (n-1)] feature and output means / scales
     bool has_mlp = false;

@@ -69,6 +69,53 @@ def test_hessian_matches_definition(K, mode, tol, N, order):
 
 
 @pytest.mark.parametrize("mode", MIXED)
+@pytest.mark.parametrize("N,order", [(1, 4), (3, 20), (5, 30)])
+def test_mixed_gradient_moments_are_fp64(K, mode, N, order):
+    """The mixed sweep's FP64 part: column 0 of H is m_0 <m exp(alpha.m)>, the ansatz moments
+    (m_0 is constant), which the mixed modes form in FP64 with the scaled exponential and never
+    from the tensor cores. Against the oracle's full rule for peaked vMF states: 1e-14 + 16 eps
+    max_q sum_c |alpha_c m_c(q)| relative (the exponent is a sum of terms of that size, formed
+    with a few roundings after scaling, and its absolute error is the exponential's relative one;
+    1e-14 covers the exponential's own error; a TF32 or BF16 path would be off by 1e-7 or more);
+    and, for exponents that are one constant z per cell, exp(z) within 1e-14 + 4|z| 2^-52
+    relative over z in [-720, 80], which reaches the range test's slow path below -512 and gives
+    exactly 0 below -707."""
+    m = synth.jittered_mesh(18, 0.0, 1.0, seed=3)
+    mesh = K.Mesh(m.xy, m.tri)
+    C = mesh.ncells
+    s = K.MNSolver(mesh, N, order, mode=mode)
+    T = O.Tables(N, order)
+    u = vmf_u(T, C, seed=60 + N, kappa_hi=50.0)
+    a = O.isotropic_alpha(T, u)
+    O.closure(T, u, a)
+    Hg = s.hessian(dev(a)).cpu().numpy()
+    col = np.empty((C, T.n))
+    cond = np.empty(C)
+    for i in range(C):
+        col[i] = T.M.T @ (T.w * np.exp(T.M @ a[i]) * T.M[:, 0])
+        cond[i] = np.abs(T.M * a[i]).sum(axis=1).max()
+    rel = np.abs(Hg[:, :, 0] - col).max(axis=1) / np.abs(col).max(axis=1)
+    bound = 1e-14 + 16.0 * 2.0 ** -52 * cond
+    print("column 0 rel err: max", rel.max(), "median", np.median(rel), "max err/bound", (rel / bound).max())
+    assert (rel <= bound).all(), (rel / bound).max()
+    # constant exponent per cell: alpha = (z / m_0, 0, ...)
+    m0 = T.M[0, 0]
+    z = np.concatenate([np.random.default_rng(8).uniform(-720.0, 80.0, C - 5),
+                        [0.0, -706.9, -707.5, -513.0, 79.0]])
+    al = np.zeros((C, T.n))
+    al[:, 0] = z / m0
+    H00 = s.hessian(dev(al)).cpu().numpy()[:, 0, 0]
+    norm = float((T.w * T.M[:, 0] ** 2).sum())
+    ref = np.exp(z) * norm
+    live = z > -707.0
+    rel = np.abs(H00[live] - ref[live]) / ref[live]
+    bound = 1e-14 + 4.0 * np.abs(z[live]) * 2.0 ** -52
+    print("constant exponent: max rel err", rel.max(), "max err/bound", (rel / bound).max())
+    assert (rel <= bound).all(), (rel / bound).max()
+    assert (H00[z < -707.1] == 0).all()
+
+
+@pytest.mark.parametrize("mode", MIXED)
 @pytest.mark.parametrize("N,order", [(2, 10), (3, 20), (5, 30)])
 def test_mixed_closure_matches_oracle(K, mode, N, order):
     T = O.Tables(N, order)
