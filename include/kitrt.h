@@ -54,7 +54,10 @@ typedef enum {
 enum {
     KITRT_FP64 = 0,        /* every sum, factorisation and line search in FP64 */
     KITRT_MIXED_TF32 = 1,  /* Hessian-only moment sums on tensor cores (TF32 in, FP32 accumulate);
-                              exponent, exp, gradient, objective, Cholesky, line search in FP64 */
+                              exponent, gradient, objective and line search in FP64 (the exp to
+                              about 1e-14 relative, its small polynomial term in FP32); the Newton
+                              step's Hessian assembly and Cholesky in FP32, in FP64 for cells
+                              handed over */
     KITRT_MIXED_BF16 = 2,  /* as MIXED_TF32 with BF16 tensor-core inputs */
     KITRT_LEARNED = 3      /* MLP prediction of alpha, exact mass fix, FP64 residual check, Newton
                               (mixed Hessian) only for cells whose residual exceeds fallback_tol */
