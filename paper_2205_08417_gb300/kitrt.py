@@ -118,7 +118,7 @@ def _lib():
         path = _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"kitrt CUDA library not built ({path}); run "
-                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+                               "`python -m paper_2205_08417_gb300.build`")
         L = C.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(L, name)
