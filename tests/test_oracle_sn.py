@@ -2,7 +2,8 @@
 O Sigma M of the scattering operator; Sec. 4.2/4.4: explicit upwind step per ordinate). Checked
 against: the oracle's M_N flux update (itself pinned by a hand-written step), which the moments of
 an S_N step must reproduce; the addition theorem of spherical harmonics, which turns O Sigma M into
-a direct sum over the scattering kernel's Legendre series; and closed-form uniform states."""
+a direct sum over the scattering kernel's Legendre series; closed-form uniform states; and
+equivariance under mirroring the mesh (3e-16)."""
 import math
 
 import numpy as np
@@ -126,3 +127,27 @@ def test_sn_run_conserves_mass_up_to_boundary_outflow():
     O.sn_run(T, G, p2, z, np.full(G.C, 0.5), z, dt, 2, bc=1)
     ref = O.sn_step(T, G, out, z, np.full(G.C, 0.5), z, dt, bc=1)
     np.testing.assert_array_equal(p2, ref)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_sn_step_commutes_with_mirroring_the_mesh(bc, axis):
+    """The S_N step (Eq. SNEqns2, Sec. 4.4 upwind flux per ordinate) on the mesh mirrored in x or y,
+    from the ordinates carried to the mirrored directions, equals the mirrored step, with
+    anisotropic scattering; pins the per-ordinate upwind choice for clockwise triangles."""
+    from mirror_map import mirror_points, mirror_xy
+    N, order = 3, 8
+    T = O.Tables(N, order)
+    m = synth.jittered_mesh(9, -1.0, 1.0, seed=2)
+    G, Gr = O.Geometry(m.xy, m.tri), O.Geometry(mirror_xy(m.xy, axis), m.tri)
+    mu, phi, w, ox, oy = O.quadrature(order)
+    perm = mirror_points(ox, oy, mu, axis)
+    rng = np.random.default_rng(4)
+    psi = rng.uniform(0.1, 2.0, size=(G.C, T.Q))
+    sa, ss, q = rng.uniform(0, 1, G.C), rng.uniform(0, 2, G.C), rng.uniform(0, 0.5, G.C)
+    g = [1.0, 0.6, 0.3, 0.1]
+    dt = G.cfl_dt(0.4)
+    a = O.sn_run(T, G, psi.copy(), sa, ss, q, dt, 3, g=g, bc=bc)
+    b = O.sn_run(T, Gr, psi[:, perm].copy(), sa, ss, q, dt, 3, g=g, bc=bc)
+    print("S_N mirror diff", np.abs(b - a[:, perm]).max() / np.abs(a).max())
+    assert np.abs(b - a[:, perm]).max() <= 1e-14 * np.abs(a).max()
