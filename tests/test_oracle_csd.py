@@ -180,3 +180,33 @@ def test_dose_of_uniform_fluence_does_not_depend_on_density():
     # step dt spans dE = S_w dt of energy
     expect = dt * sum(Sn * Sn for Sn in S) * psi * 4 * math.pi
     np.testing.assert_allclose(dose, expect, rtol=1e-14)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_density_step_commutes_with_mirroring_the_mesh(bc, axis):
+    """The transformed CSD step (psi~ / rho transported, Sec. 2) on the mesh mirrored in x or y,
+    with each cell keeping its density and moments carried to the mirrored directions, equals the
+    mirrored step (3 steps, two tissues)."""
+    from mirror_map import mirror_basis, mirror_points, mirror_xy
+    N, order = 2, 10
+    T = O.Tables(N, order)
+    m = synth.jittered_mesh(10, -1.5, 1.5, seed=3)
+    G, Gr = O.Geometry(m.xy, m.tri), O.Geometry(mirror_xy(m.xy, axis), m.tri)
+    mu, phi, w, ox, oy = O.quadrature(order)
+    D = mirror_basis(T.M, mirror_points(ox, oy, mu, axis))
+    rho = synth.two_tissue_density(G.cen)
+    c, k, wt = synth.vmf_mixtures(G.C, 21)
+    u = (synth.vmf_density(np.stack([ox, oy, mu], axis=1), c, k, wt) @ (T.w[:, None] * T.M)) * rho[:, None]
+    rng = np.random.default_rng(21)
+    sa, ss, q = rng.uniform(0, 1, G.C), rng.uniform(0, 2, G.C), rng.uniform(0, 0.5, G.C)
+    dt = 0.4 * G.cfl_dt(1.0) * rho.min()
+    u1 = u.copy()
+    a1 = O.isotropic_alpha(T, u1)
+    assert O.mn_run_rho(T, G, rho, u1, a1, sa, ss, q, dt, 3, bc=bc)[0] == 0
+    ur = u @ D.T
+    ar = O.isotropic_alpha(T, ur)
+    assert O.mn_run_rho(T, Gr, rho, ur, ar, sa, ss, q, dt, 3, bc=bc)[0] == 0
+    err = np.linalg.norm(ur - u1 @ D.T) / np.linalg.norm(u1)
+    print("density mirror diff", err)
+    assert err <= 1e-12

@@ -111,3 +111,29 @@ def test_isotropic_closed_form_is_unchanged_by_regularization():
     st, _ = O.closure_reg(T, u, a, 1e-3, 1, tau=1e-13, polish=False)
     assert (st == 0).all()
     np.testing.assert_allclose(a, ref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("reg0", [0, 1])
+def test_regularized_closure_commutes_with_the_rules_mirrors(reg0):
+    """The penalty gamma/2 |alpha_reg|^2 of Eq. entropyOCP_reg / _part_reg is invariant under the
+    product rule's mirrors, which act on the basis as an orthogonal D that keeps m_0, so the
+    regularized minimiser moves with the state: alpha(D u) = D alpha(u)."""
+    from mirror_map import mirror_basis, mirror_points
+    N, order = 3, 12
+    T = O.Tables(N, order)
+    mu, phi, w, ox, oy = O.quadrature(order)
+    c, k, wt = synth.vmf_mixtures(32, 5)
+    u = synth.vmf_density(np.stack([ox, oy, mu], axis=1), c, k, wt) @ (T.w[:, None] * T.M)
+    a = O.isotropic_alpha(T, u)
+    st, _ = O.closure_reg(T, u, a, 1e-2, reg0=reg0)
+    for axis in (0, 1):
+        D = mirror_basis(T.M, mirror_points(ox, oy, mu, axis))
+        assert abs(D[0, 0] - 1.0) < 1e-12
+        ur = u @ D.T
+        ar = O.isotropic_alpha(T, ur)
+        st_r, _ = O.closure_reg(T, ur, ar, 1e-2, reg0=reg0)
+        ok = (st == 0) & (st_r == 0)
+        assert ok.mean() > 0.9
+        err = np.linalg.norm(ar[ok] - a[ok] @ D.T, axis=1) / np.linalg.norm(a[ok], axis=1)
+        print("regularized mirror diff", err.max())
+        assert err.max() <= 1e-10
