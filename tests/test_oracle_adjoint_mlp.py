@@ -1,6 +1,7 @@
 """Pins for the oracle's discrete adjoint (checked against central finite differences of its own
-forward objective, which is a different code path) and for its MLP backward pass and Adam step
-(finite differences; Adam's first step has the closed form -lr * sign(g))."""
+forward objective, which is a different code path, and against the mirror image of the same
+problem) and for its MLP backward pass and Adam step (finite differences; Adam's first step has
+the closed form -lr * sign(g))."""
 import numpy as np
 import pytest
 
@@ -161,3 +162,22 @@ def test_adam_second_step_closed_forms():
         O.adam(p, g, m, v, 1, lr=lr, b1=b1, b2=b2, eps=0.0)
         O.adam(p, g2, m, v, 2, lr=lr, b1=b1, b2=b2, eps=0.0)
         np.testing.assert_allclose(p, expect, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_adjoint_is_unchanged_by_mirroring_the_mesh(axis):
+    """The same block problem on the mesh mirrored in x or y (every triangle clockwise, each cell
+    keeping its block, source and target flag) is the mirror image of the original: the
+    isotropic start is its own mirror, so the objective and every block gradient of the adjoint
+    (transposed flux, closure backward) must be unchanged."""
+    from mirror_map import mirror_xy
+    T, G, blk, sa, ss, q, tgt, u0, a0 = _blocks_problem()
+    m = synth.jittered_mesh(13, 0.0, 7.0, seed=3)
+    Gr = O.Geometry(mirror_xy(m.xy, axis), m.tri)
+    dt = G.cfl_dt(0.4)
+    J, gsa, gss = O.mn_adjoint(T, G, blk, sa, ss, q, tgt, dt, 8, u0, a0.copy(), bc=1, tau=1e-13)
+    Jr, gsar, gssr = O.mn_adjoint(T, Gr, blk, sa, ss, q, tgt, dt, 8, u0, a0.copy(), bc=1, tau=1e-13)
+    scale = max(np.abs(gsa).max(), np.abs(gss).max())
+    print("adjoint mirror: J", abs(Jr - J) / abs(J), "grad", max(np.abs(gsar - gsa).max(), np.abs(gssr - gss).max()) / scale)
+    assert abs(Jr - J) <= 1e-13 * abs(J)
+    assert np.abs(gsar - gsa).max() <= 1e-12 * scale and np.abs(gssr - gss).max() <= 1e-12 * scale
